@@ -1,0 +1,470 @@
+#!/usr/bin/env python3
+"""Benchmark of the batched parallel-prefix hot path on one GB300 per rank.
+
+One step = one pass of every data-path row over synthetic batches shaped like
+the paper's workloads (Section VI: batches of problems of power-of-two size,
+float32, data resident on the GPU):
+
+  fft      complex64 Stockham FFT, forward and inverse, N in {16, 64, 256,
+           1024, 4096}, batch = 2^24 / N signals each
+  tridiag  float32 CR/PCR solve, n in {64, 256, 1024, 2048}, 2^24 unknowns each
+  refined  float64-residual refined solve, n = 1024, 2^14 systems
+  scan     inclusive sum scan, int32 and float32, n in {64, 1024, 8192},
+           2^26 elements each
+
+Every buffer pair is larger than the 129 MB L2, and consecutive launches touch
+different buffers, so no L2 flush is needed between them.  `value` is the
+total elements processed per second (Gelem/s) over all ranks.  Plans are the
+library's query_plan choice (tuned cache if present, else the analytical
+guideline).
+
+--impl reference times the CPU oracle (test infrastructure) on a bounded
+sample of the same workload and prints the same line with "impl": "reference".
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import seeded_inputs as si  # noqa: E402
+
+FFT_SIZES = [16, 64, 256, 1024, 4096]
+TRI_SIZES = [64, 256, 1024, 2048]
+SCAN_SIZES = [64, 1024, 8192]
+FFT_TOTAL = 1 << 24
+TRI_TOTAL = 1 << 24
+SCAN_TOTAL = 1 << 26
+REF_N, REF_BATCH = 1024, 1 << 14
+
+METRIC = "batched scan/FFT/tridiag Gelem/s, %HBM roofline; tuned vs exhaustive-best"
+WORKLOAD = ("fft c2c fwd+inv N=16..4096 batch=2^24/N; tridiag CR/PCR n=64..2048 2^24 unknowns; "
+            "refined n=1024 x 2^14; scan i32+f32 n=64,1024,8192 x 2^26")
+
+
+def read_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.lines:
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax = float(parts[2])
+            except ValueError:
+                continue
+            for name, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+# ----------------------------------------------------------------- workload
+
+class Workload:
+    """Device buffers for every row of the step, filled from the seeded generators."""
+
+    def __init__(self, torch, bp, dev, scale: float = 1.0):
+        self.torch, self.bp, self.dev = torch, bp, dev
+        self.items = []  # (name, op_label, n, batch, elems, bytes, launch_fn, host_in, host_out)
+        t = torch
+        for n in FFT_SIZES:
+            batch = max(1, int(FFT_TOTAL * scale) // n)
+            z = si.fft_c64(batch, n, stream=100 + n)
+            zin = t.from_numpy(z.view(np.float32).reshape(-1)).to(dev)
+            zout = t.empty_like(zin)
+            for direction, tag in ((-1, "fwd"), (1, "inv")):
+                self._add("fft_%s_%d" % (tag, n), "fft", n, batch, batch * n, 16 * batch * n,
+                          (lambda zi=zin, zo=zout, n=n, b=batch, d=direction:
+                           bp.fft_batched(zi, zo, n, b, d)), [zin], [zout])
+        for n in TRI_SIZES:
+            batch = max(1, int(TRI_TOTAL * scale) // n)
+            a, b, c, d, _ = si.tridiag_f32(batch, n, stream=200 + n)
+            ts = [t.from_numpy(v).to(dev) for v in (a, b, c, d)]
+            x = t.empty_like(ts[0])
+            self._add("tridiag_%d" % n, "tridiag", n, batch, batch * n, 20 * batch * n,
+                      (lambda ts=ts, x=x, n=n, b=batch: bp.tridiag_batched(*ts, x, n, b)), ts, [x])
+        batch = max(1, int(REF_BATCH * scale))
+        a, b, c, d, _ = si.tridiag_f32(batch, REF_N, seed=si.CONFIG_SEEDS["precision"])
+        ts = [t.from_numpy(v).to(dev) for v in (a, b, c, d)]
+        x64 = t.empty((batch, REF_N), dtype=t.float64, device=dev)
+        self._add("refined_%d" % REF_N, "refined", REF_N, batch, batch * REF_N, 24 * batch * REF_N,
+                  (lambda ts=ts, x=x64, b=batch: bp.tridiag_refined(*ts, x, REF_N, b)), ts, [x64])
+        for dname, gen in (("i32", lambda b, n: si.scan_i32(b, n, stream=300 + n)),
+                           ("f32", lambda b, n: si.scan_f32(b, n, stream=400 + n))):
+            for n in SCAN_SIZES:
+                batch = max(1, int(SCAN_TOTAL * scale) // n)
+                xin = t.from_numpy(gen(batch, n)).to(dev)
+                xout = t.empty_like(xin)
+                self._add("scan_%s_%d" % (dname, n), "scan_" + dname, n, batch, batch * n, 8 * batch * n,
+                          (lambda xi=xin, xo=xout, n=n, b=batch: bp.scan_batched(xi, xo, n, b)), [xin], [xout])
+
+    def _add(self, name, op, n, batch, elems, nbytes, fn, ins, outs):
+        self.items.append(dict(name=name, op=op, n=n, batch=batch, elems=elems, bytes=nbytes, fn=fn,
+                               ins=ins, outs=outs))
+
+    @property
+    def elems(self):
+        return sum(i["elems"] for i in self.items)
+
+
+def run_ours(args):
+    import torch
+    world, rank, local = dist_setup()
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    dev = torch.device("cuda", local if world > 1 else 0)
+    torch.cuda.set_device(dev)
+    import paper_2310_16214_gb300 as bp
+
+    wl = Workload(torch, bp, dev, scale=args.scale)
+    stream = torch.cuda.current_stream()
+    ev = {it["name"]: [] for it in wl.items}
+
+    def step(record: bool):
+        for it in wl.items:
+            if record:
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                it["fn"]()
+                e1.record(stream)
+                ev[it["name"]].append((e0, e1))
+            else:
+                it["fn"]()
+
+    for _ in range(args.warmup):
+        step(False)
+    torch.cuda.synchronize()
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    sampler = ClockSampler(local if world > 1 else 0)
+    sampler.start()
+    time.sleep(0.3)
+    barrier()
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    for _ in range(args.steps):
+        step(True)
+    t1.record(stream)
+    barrier()
+    clocks = sampler.stop()
+    total_ms = t0.elapsed_time(t1)
+    if world > 1:
+        import torch.distributed as dist
+        tt = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        total_ms = float(tt.item())
+
+    per_item = {}
+    for it in wl.items:
+        ms = [a.elapsed_time(b) for a, b in ev[it["name"]]]
+        per_item[it["name"]] = statistics.mean(ms)
+    per_op = {}
+    for it in wl.items:
+        d = per_op.setdefault(it["op"], {"ms": 0.0, "elems": 0, "bytes": 0})
+        d["ms"] += per_item[it["name"]]
+        d["elems"] += it["elems"]
+        d["bytes"] += it["bytes"]
+    peak, peak_kind = read_peaks()
+    for k, d in per_op.items():
+        d["gelem_s"] = d["elems"] / (d["ms"] * 1e-3) / 1e9
+        d["gb_s"] = d["bytes"] / (d["ms"] * 1e-3) / 1e9
+        d["hbm_frac"] = d["gb_s"] / peak
+        d["ms"] = round(d["ms"], 4)
+    # dominant kernel: the launch with the largest share of the step
+    dom = max(wl.items, key=lambda it: per_item[it["name"]])
+    dom_ms = per_item[dom["name"]]
+    achieved = dom["bytes"] / (dom_ms * 1e-3) / 1e9
+    roofline = {"bound": "hbm", "kernel": dom["name"], "achieved": round(achieved, 1), "peak": peak,
+                "peak_kind": peak_kind, "unit": "GB/s", "frac": round(achieved / peak, 4),
+                "traffic": None, "algorithmic_bytes": dom["bytes"], "launch_ms": round(dom_ms, 5)}
+    step_ms = total_ms / args.steps
+    value = world * wl.elems / (step_ms * 1e-3) / 1e9
+    launches_per_step = len(wl.items)
+    items_out = {it["name"]: {"ms": round(per_item[it["name"]], 5),
+                              "gb_s": round(it["bytes"] / (per_item[it["name"]] * 1e-3) / 1e9, 1)}
+                 for it in wl.items}
+
+    e2e = measure_e2e(torch, wl, stream, args) if rank == 0 and not args.no_e2e else None
+    cpu = cpu_baseline(args) if (rank == 0 and world == 1 and not args.no_cpu) else None
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": round(value, 3), "unit": "Gelem/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(step_ms, 4),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32 (fft, tridiag, scan f32), i32 (scan), f64 residual (refined)",
+            "data": "synthetic (seeded SplitMix64, paper-shaped batches)",
+            "config": {"workload": WORKLOAD, "elems_per_step_per_gpu": wl.elems,
+                       "l2": "inputs larger than L2 (every buffer pair > 129 MB), no flush",
+                       "plans": "query_plan (analytical guideline unless a tuned plan is cached)",
+                       "parallelism": "replicas" if world > 1 else "single"},
+            "roofline": roofline, "per_op": per_op, "per_launch": items_out,
+            "gpu_launches": launches_per_step * args.steps, "clocks": clocks,
+            "e2e": e2e, "cpu_baseline": cpu,
+        }
+        print(json.dumps(line))
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def measure_e2e(torch, wl, stream, args):
+    """Same step through the public API with host buffers: pinned host inputs
+    copied to the device, the kernels, and the outputs copied back, all inside
+    the timed region."""
+    host_in = {}
+    host_out = {}
+    h2d = d2h = 0
+    for it in wl.items:
+        host_in[it["name"]] = [x.cpu().pin_memory() for x in it["ins"]]
+        host_out[it["name"]] = [torch.empty(x.shape, dtype=x.dtype).pin_memory() for x in it["outs"]]
+        h2d += sum(x.numel() * x.element_size() for x in it["ins"])
+        d2h += sum(x.numel() * x.element_size() for x in it["outs"])
+    # inputs shared between fwd and inv FFT rows are copied once per row, as a
+    # user calling each row independently would
+
+    def step():
+        for it in wl.items:
+            for hx, dx in zip(host_in[it["name"]], it["ins"]):
+                dx.copy_(hx, non_blocking=True)
+            it["fn"]()
+            for hx, dx in zip(host_out[it["name"]], it["outs"]):
+                hx.copy_(dx, non_blocking=True)
+
+    steps = max(1, min(args.steps, 5))
+    step()
+    torch.cuda.synchronize()
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    for _ in range(steps):
+        step()
+    t1.record(stream)
+    torch.cuda.synchronize()
+    ms = t0.elapsed_time(t1) / steps
+    return {"value": round(wl.elems / (ms * 1e-3) / 1e9, 3), "unit": "Gelem/s", "ms_per_step": round(ms, 3),
+            "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "steps": steps}
+
+
+# ----------------------------------------------------------- CPU oracle leg
+
+def oracle_sample(sample_rows: int):
+    """A bounded sample of every row of the step (inputs only)."""
+    items = []
+    for n in FFT_SIZES:
+        rows = max(1, sample_rows * 64 // n)
+        z = si.fft_c64(rows, n, stream=100 + n)
+        items.append(("fft", -1, z))
+        items.append(("fft", +1, z))
+    for n in TRI_SIZES:
+        rows = max(1, sample_rows * 64 // n)
+        items.append(("thomas", 0, si.tridiag_f32(rows, n, stream=200 + n)[:4]))
+    items.append(("thomas", 0, si.tridiag_f32(max(1, sample_rows // 16), REF_N,
+                                              seed=si.CONFIG_SEEDS["precision"])[:4]))
+    for n in SCAN_SIZES:
+        rows = max(1, sample_rows * 256 // n)
+        items.append(("scan_i32", 0, si.scan_i32(rows, n, stream=300 + n)))
+        items.append(("scan_f32", 0, si.scan_f32(rows, n, stream=400 + n)))
+    return items
+
+
+def oracle_run(items):
+    """Run the CPU oracle on a prepared sample; returns (elements, seconds)."""
+    import oracle
+    elems = 0
+    t0 = time.perf_counter()
+    for kind, arg, x in items:
+        if kind == "fft":
+            oracle.fft(x, arg)
+            elems += x.size
+        elif kind == "thomas":
+            oracle.thomas(*x)
+            elems += x[1].size
+        elif kind == "scan_i32":
+            oracle.scan_i32(x)
+            elems += x.size
+        else:
+            oracle.scan_f32(x)
+            elems += x.size
+    return elems, time.perf_counter() - t0
+
+
+def cpu_baseline(args):
+    items = oracle_sample(args.cpu_rows)
+    elems, secs = oracle_run(items)
+    return {"value": round(elems / secs / 1e9, 6), "unit": "Gelem/s", "cores": 1, "kind": "oracle",
+            "sample": "%d elements across every row of the step (%d x 64 elements per FFT and tridiag size, "
+                      "x 256 per scan size), single-threaded C oracle, %.1f s" % (elems, args.cpu_rows, secs)}
+
+
+def run_reference(args):
+    world, rank, local = dist_setup()
+    if rank != 0:
+        return
+    items = oracle_sample(max(1, args.cpu_rows // 16))
+    for _ in range(args.warmup):
+        oracle_run(items)
+    elems = 0
+    secs = 0.0
+    for _ in range(args.steps):
+        e, s = oracle_run(items)
+        elems += e
+        secs += s
+    value = elems / secs / 1e9
+    line = {
+        "impl": "reference", "metric": METRIC, "value": round(value, 6), "unit": "Gelem/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(1e3 * secs / args.steps, 3),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64 (oracle)",
+        "data": "synthetic (seeded SplitMix64, paper-shaped batches)",
+        "config": {"workload": WORKLOAD, "sample": "bounded per-step sample of every row"},
+        "cpu_baseline": {"value": round(value, 6), "unit": "Gelem/s", "kind": "oracle", "cores": 1,
+                         "sample": "%d elements per step" % (elems // max(1, args.steps))},
+        "e2e": {"value": round(value, 6), "unit": "Gelem/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+
+
+def tune_report(args):
+    """Tuned vs exhaustive (Section VI): for every op and size of the step, the
+    analytical plan, the learned-cost-model (BO) plan and the exhaustive best,
+    each re-timed back to back; e_i = t_best / t_plan and Phi per op."""
+    import torch
+    torch.cuda.set_device(0)
+    import paper_2310_16214_gb300 as bp
+    peak, _ = read_peaks()
+    cases = [("fft", bp.OP_FFT, bp.F32, n, FFT_TOTAL // n, 16) for n in FFT_SIZES]
+    cases += [("tridiag", bp.OP_TRIDIAG, bp.F32, n, TRI_TOTAL // n, 20) for n in TRI_SIZES]
+    cases += [("refined", bp.OP_TRIDIAG_REFINED, bp.F32, REF_N, REF_BATCH, 24)]
+    cases += [("scan_i32", bp.OP_SCAN, bp.I32, n, SCAN_TOTAL // n, 8) for n in SCAN_SIZES]
+    cases += [("scan_f32", bp.OP_SCAN, bp.F32, n, SCAN_TOTAL // n, 8) for n in SCAN_SIZES]
+    if args.ops:
+        keep = set(args.ops.split(","))
+        cases = [c for c in cases if c[0] in keep]
+    rows = []
+    for name, op, dt, n, batch, bpe in cases:
+        t0 = time.time()
+        pa, _ = bp.tune_plan(op, dt, n, batch, bp.TUNE_ANALYTIC)
+        pl, rl = bp.tune_plan(op, dt, n, batch, bp.TUNE_LEARNED, budget=args.bo_budget, seed=args.seed)
+        pe, re_ = bp.tune_plan(op, dt, n, batch, bp.TUNE_EXHAUSTIVE)
+        ta = bp.time_plan(pa, dt, n, batch, args.reps)
+        tl = bp.time_plan(pl, dt, n, batch, args.reps)
+        te = bp.time_plan(pe, dt, n, batch, args.reps)
+        best = min(ta, tl, te)
+        row = {"op": name, "n": n, "batch": batch, "space": re_.space_size,
+               "analytic": {"plan": pa.as_dict(), "ms": round(ta, 5), "e": round(best / ta, 4)},
+               "learned": {"plan": pl.as_dict(), "ms": round(tl, 5), "e": round(best / tl, 4),
+                           "evaluations": rl.evaluations},
+               "exhaustive": {"plan": pe.as_dict(), "ms": round(te, 5), "evaluations": re_.evaluations},
+               "best_gb_s": round(bpe * n * batch / (best * 1e-3) / 1e9, 1),
+               "best_hbm_frac": round(bpe * n * batch / (best * 1e-3) / 1e9 / peak, 4),
+               "seconds": round(time.time() - t0, 1)}
+        rows.append(row)
+        print(json.dumps(row), flush=True)
+    ops = sorted(set(r["op"] for r in rows))
+    summary = {}
+    for o in ops:
+        rs = [r for r in rows if r["op"] == o]
+        summary[o] = {"phi_analytic": round(bp.phi([r["analytic"]["e"] for r in rs]), 4),
+                      "phi_learned": round(bp.phi([r["learned"]["e"] for r in rs]), 4),
+                      "bo_evaluations": [r["learned"]["evaluations"] for r in rs],
+                      "space": [r["space"] for r in rs]}
+    print(json.dumps({"tune_report": summary}))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--scale", type=float, default=1.0, help="fraction of the full batch sizes (testing only)")
+    ap.add_argument("--cpu-rows", type=int, default=131072)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--tune-report", action="store_true", help="tuned vs exhaustive Phi report instead of the bench")
+    ap.add_argument("--ops", default="", help="comma-separated ops for --tune-report")
+    ap.add_argument("--reps", type=int, default=50)
+    ap.add_argument("--bo-budget", type=int, default=40)
+    ap.add_argument("--seed", type=int, default=1)
+    args = ap.parse_args()
+    if args.tune_report:
+        tune_report(args)
+    elif args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,283 @@
+/*
+ * bplg.h -- C ABI of the GB300 batched parallel-prefix library.
+ *
+ * The library computes three families of batched parallel-prefix operations
+ * (Section III of "Performance Tuning for GPU-Embedded Systems: Machine-
+ * Learning-based and Analytical Model-driven Tuning Methodologies", Dieguez
+ * and Amor, 2023) with hand-written sm_103a CUDA kernels, and the two tuning
+ * methodologies of Section IV that choose their performance parameters:
+ *
+ *   scan     inclusive sum scan, int32 (wrap-around) and float32
+ *   FFT      complex Stockham FFT of power-of-two length, radix 2/4/8/16
+ *   tridiag  cyclic reduction + parallel cyclic reduction (CR/PCR) hybrid,
+ *            and the same solver wrapped in float64-residual refinement
+ *   tuning   analytical guideline (Section IV-A), Bayesian optimisation with a
+ *            Gaussian-process cost model (Section IV-B), exhaustive search and
+ *            the Phi metric (Section VI)
+ *
+ * Conventions for every entry point
+ *   - Return value: BPLG_OK (0) or a negative BPLG_ERR_* code; the message of
+ *     the last error on the calling thread is returned by bplg_last_error().
+ *   - Memory: the caller owns every buffer and every stream.  "device" buffers
+ *     are CUDA global memory of the current device; "host" buffers are CPU
+ *     memory.  Compute entry points never allocate on their hot path; the
+ *     first FFT call on a device allocates the shared twiddle table (256 KB)
+ *     once, synchronously, so it must not be the first call inside a stream
+ *     capture.
+ *   - Layout: batched data is row-major [batch][n], problem after problem,
+ *     with no padding between problems.  Device pointers must be 16-byte
+ *     aligned.
+ *   - Streams: `stream` is a cudaStream_t passed as void* (NULL = the legacy
+ *     default stream).  Compute entry points are asynchronous on it; argument
+ *     errors are reported before anything is enqueued.
+ *   - Plans: a NULL plan means "the plan bplg_query_plan returns".  A non-NULL
+ *     plan is validated against the size and the device; an unusable plan
+ *     returns BPLG_ERR_INVALID_PLAN without launching.
+ */
+#ifndef BPLG_H
+#define BPLG_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ------------------------------------------------------------ error codes */
+#define BPLG_OK 0
+#define BPLG_ERR_INVALID_ARG (-1)      /* null pointer, n/batch out of range, misaligned pointer */
+#define BPLG_ERR_UNSUPPORTED_SIZE (-2) /* n not a power of two or above the kernel's maximum */
+#define BPLG_ERR_INVALID_PLAN (-3)     /* plan does not fit the size or the device limits */
+#define BPLG_ERR_CUDA (-4)             /* a CUDA runtime call failed; see bplg_last_error() */
+#define BPLG_ERR_TIMEOUT (-5)          /* a tuning candidate exceeded its wall-clock limit */
+#define BPLG_ERR_DEVICE_FLAG (-6)      /* a kernel reported a device-side failure */
+#define BPLG_ERR_NO_DEVICE (-7)        /* no CUDA device is visible */
+
+/* ----------------------------------------------------------------- enums */
+typedef enum { BPLG_I32 = 0, BPLG_F32 = 1 } bplg_dtype;
+
+typedef enum {
+    BPLG_OP_SCAN = 0,            /* Section III, scan primitive */
+    BPLG_OP_FFT = 1,             /* Section III, Stockham FFT */
+    BPLG_OP_TRIDIAG = 2,         /* Section III, tridiagonal solver (CR/PCR hybrid) */
+    BPLG_OP_TRIDIAG_REFINED = 3, /* the solver inside float64-residual refinement */
+    BPLG_OP_FFT_TC = 4           /* FFT whose radix-16 stages run on tensor cores */
+} bplg_op;
+
+typedef enum { BPLG_PATTERN_KS = 0, BPLG_PATTERN_LF = 1 } bplg_scan_pattern;
+typedef enum { BPLG_TUNE_ANALYTIC = 0, BPLG_TUNE_LEARNED = 1, BPLG_TUNE_EXHAUSTIVE = 2 } bplg_tune_method;
+typedef enum { BPLG_TC_BF16 = 0, BPLG_TC_F16 = 1 } bplg_tc_precision;
+
+/* --------------------------------------------------------------- the plan
+ * The performance parameters B of Section IV-B ("Table I"): the (S, P, L)
+ * tuple of Section IV-A plus the radix, the shuffle switch and the layout
+ * knobs.  A plain value: copy it, store it, compare it with memcmp.
+ *
+ *   P       elements per thread.  For the FFT P equals the radix r.
+ *   L       threads per block = spb * (n / P).
+ *   spb     problems (signals or systems) per block.
+ *   S       shared-memory elements per block (derived, reported).
+ *   radix   FFT radix r in {2,4,8,16}; 2 for scan and tridiag.
+ *   shuffle tridiag: the PCR phase runs in one warp with shuffles (cr_switch
+ *           <= 32); scan: always 1 (warp-shuffle prefix stages).
+ *   pattern scan: prefix circuit of the shuffle stages, BPLG_PATTERN_KS or
+ *           BPLG_PATTERN_LF (Fig. 1(f) / 1(d)).
+ *   smem_layout FFT: 0 interleaved complex, 1 real and imaginary parts
+ *           exchanged in turn through one float buffer (Section V-C).
+ *   smem_pad 1: pad shared-memory rows against bank conflicts.
+ *   io      FFT: 0 registers <-> global memory directly, 1 staged through
+ *           shared memory with 16-byte accesses.
+ *   cr_switch tridiag: system size m at which cyclic reduction hands over to
+ *           parallel cyclic reduction (1 = pure CR, n = pure PCR).
+ */
+typedef struct {
+    int32_t op;
+    int32_t n;
+    int32_t P;
+    int32_t L;
+    int32_t spb;
+    int32_t S;
+    int32_t radix;
+    int32_t shuffle;
+    int32_t pattern;
+    int32_t smem_layout;
+    int32_t smem_pad;
+    int32_t io;
+    int32_t cr_switch;
+    int32_t reserved[3];
+} bplg_plan;
+
+/* -------------------------------------------------------- compute calls */
+
+/* Batched inclusive sum scan (Section III, "Scan Operator"): for every
+ * problem s, out[s][i] = in[s][0] + ... + in[s][i].
+ *   dtype  BPLG_I32 (two's-complement wrap-around, bit-exact) or BPLG_F32.
+ *   in,out device, [batch][n] of dtype; in == out (in place) is allowed.
+ *   n      power of two, 1 <= n <= 32768; batch >= 1.
+ * Errors: INVALID_ARG, UNSUPPORTED_SIZE, INVALID_PLAN, CUDA. */
+int bplg_scan_batched(int32_t dtype, const void *in, void *out, int64_t n, int64_t batch,
+                      const bplg_plan *plan, void *stream);
+
+/* Batched complex FFT by the Stockham self-sorting algorithm (Section III,
+ * "Fast Fourier Transform", Fig. 1(c)): X[k] = sum_j x[j] exp(dir*2*pi*i*j*k/n)
+ * with dir = -1 (forward) or +1 (inverse, unnormalised), natural order.
+ *   in,out device, [batch][n] complex64 as interleaved (re, im) float pairs;
+ *          in == out is allowed.
+ *   n      power of two, 2 <= n <= 16384; batch >= 1.
+ * Twiddles W_M^k are generated once per device in float64 and rounded to
+ * float32.  Errors: INVALID_ARG, UNSUPPORTED_SIZE, INVALID_PLAN, CUDA. */
+int bplg_fft_batched(const void *in, void *out, int64_t n, int64_t batch, int32_t dir,
+                     const bplg_plan *plan, void *stream);
+
+/* Batched tridiagonal solve (Section III, "Tridiagonal system solvers"):
+ * a_i x_{i-1} + b_i x_i + c_i x_{i+1} = d_i for every system, by cyclic
+ * reduction down to plan->cr_switch equations, parallel cyclic reduction on
+ * those, and CR back substitution; all in float32 shared memory.
+ *   a,b,c,d device, float32 [batch][n] each (structure of arrays);
+ *           a[s][0] and c[s][n-1] are never read.
+ *   x       device, float32 [batch][n]; may alias d.
+ *   n       power of two, 2 <= n <= 8192; batch >= 1.
+ * No pivoting: the systems must be safe for elimination without pivoting
+ * (e.g. strictly diagonally dominant).  Errors: as for the scan. */
+int bplg_tridiag_batched(const float *a, const float *b, const float *c, const float *d, float *x,
+                         int64_t n, int64_t batch, const bplg_plan *plan, void *stream);
+
+/* The same solver inside iterative refinement: x0 = solve32(d); then
+ * r = d - A x_k in float64 from the stored float32 coefficients, a float32
+ * solve of the power-of-two-scaled residual, and x_{k+1} = x_k + e in
+ * float64; stop when max|e| <= tol * max|x| or after max_iter corrections.
+ *   x       device, float64 [batch][n] (must not alias the inputs).
+ *   iters   device int32 [batch] (corrections applied per system) or NULL.
+ *   n       power of two, 2 <= n <= 4096.
+ *   max_iter 0..64; tol >= 0.
+ * Errors: as for bplg_tridiag_batched. */
+int bplg_tridiag_refined(const float *a, const float *b, const float *c, const float *d, double *x,
+                         int64_t n, int64_t batch, int32_t max_iter, double tol, int32_t *iters,
+                         const bplg_plan *plan, void *stream);
+
+/* ------------------------------------------------------------- tuning */
+
+/* Per-SM limits that bound occupancy (Section IV-A: W^max, B^max, registers
+ * and shared memory). */
+typedef struct {
+    int32_t max_warps_per_sm;
+    int32_t max_blocks_per_sm;
+    int32_t regs_per_sm;
+    int32_t reg_alloc_unit;
+    int32_t warp_alloc_granularity;
+    int32_t max_regs_per_thread;
+    int32_t smem_per_sm;
+    int32_t smem_alloc_unit;
+    int32_t max_smem_per_block;
+    int32_t smem_reserved_per_block;
+    int32_t max_threads_per_block;
+    int32_t num_sms;
+} bplg_arch;
+
+/* Fill *out with the limits of device `device` (cudaGetDeviceProperties).
+ * Errors: NO_DEVICE, CUDA, INVALID_ARG. */
+int bplg_arch_query(int32_t device, bplg_arch *out);
+
+/* Fill *out with a built-in preset: 0 = GM20B (Jetson TX1, Section II),
+ * 1 = GB300.  Errors: INVALID_ARG. */
+int bplg_arch_preset(int32_t which, bplg_arch *out);
+
+/* Occupancy of one block shape (Section IV-A): active warps W_SM and active
+ * blocks B_a per SM; both 0 when the shape cannot launch.  Host only. */
+int bplg_occupancy(const bplg_arch *arch, int32_t warps_per_block, int32_t regs_per_thread,
+                   int32_t smem_per_block, int32_t *w_sm, int32_t *b_a);
+
+/* One configuration as the analytical guideline sees it. */
+typedef struct {
+    int32_t S, P, L, regs, smem, radix, shuffle, reserved;
+} bplg_candidate;
+
+/* The analytical guideline of Section IV-A (the four bullets, with the
+ * shuffle premise (i) and the radix bullet) applied to an explicit candidate
+ * list; *chosen is the index of the picked candidate, or -1 if none can
+ * launch.  Host only.  Errors: INVALID_ARG. */
+int bplg_guideline_select(const bplg_arch *arch, const bplg_candidate *cands, int32_t count,
+                          int32_t radix_tunable, int32_t *chosen);
+
+/* Phi(a, C) = |C| / sum_i 1/e_i (Section VI).  Returns 0 for an empty list
+ * or any e_i <= 0. */
+double bplg_phi(const double *efficiencies, int32_t count);
+
+/* All valid plans for (op, dtype, n) on the current device, in the library's
+ * canonical order (written up to `capacity`; *count gets the total).
+ * Validity uses the device limits and each kernel's register count from
+ * cudaFuncGetAttributes.  Errors: INVALID_ARG, UNSUPPORTED_SIZE, CUDA. */
+int bplg_enumerate_plans(int32_t op, int32_t dtype, int64_t n, bplg_plan *out, int32_t capacity,
+                         int32_t *count);
+
+/* Resources of one plan on the current device: registers per thread, dynamic
+ * + static shared memory per block, threads per block.
+ * Errors: INVALID_PLAN, CUDA. */
+int bplg_plan_resources(const bplg_plan *plan, int32_t dtype, int32_t *regs, int32_t *smem,
+                        int32_t *threads);
+
+/* Cost of one candidate in milliseconds for a caller-supplied objective;
+ * return a negative value or INFINITY for an invalid candidate. */
+typedef double (*bplg_cost_fn)(const bplg_plan *plan, void *user);
+
+typedef struct {
+    int32_t method;        /* bplg_tune_method used */
+    int32_t space_size;    /* valid plans in the search space */
+    int32_t evaluations;   /* candidate evaluations performed */
+    int32_t invalid;       /* evaluations that returned an invalid cost */
+    double chosen_ms;      /* cost of the returned plan (NaN if never evaluated) */
+    double best_seen_ms;   /* best cost among the evaluated candidates */
+} bplg_tune_report;
+
+/* The tuning problem of Section IV-B: argmin over the plans x_B of f(a_j, x_B)
+ * with a_j = (op, dtype, n, batch), where f is the median time of timed
+ * launches on the current device on library-owned buffers of that shape.
+ *   ANALYTIC    the guideline on the device limits; no GPU evaluation.
+ *   LEARNED     Bayesian optimisation: seeded random initial samples, a
+ *               Gaussian-process surrogate (Matern-5/2 on the encoded knobs,
+ *               on log time), expected improvement, stop after 5 evaluations
+ *               without improvement or at `budget` evaluations.
+ *   EXHAUSTIVE  every valid plan is timed.
+ * The result is stored in the per-process plan cache that bplg_query_plan
+ * reads.  Synchronous.  Errors: INVALID_ARG, UNSUPPORTED_SIZE, CUDA, NO_DEVICE. */
+int bplg_tune_plan(int32_t op, int32_t dtype, int64_t n, int64_t batch, int32_t method,
+                   int32_t budget, uint64_t seed, bplg_plan *out, bplg_tune_report *report);
+
+/* The same search over an explicit plan list with a caller objective (host
+ * only; used to test the search strategies without a GPU).  `arch` and
+ * `regs` (per-plan register counts, may be NULL = 32) feed the analytical
+ * method.  Errors: INVALID_ARG. */
+int bplg_tune_plans_cost(const bplg_plan *plans, int32_t count, const int32_t *regs,
+                         const int32_t *smem, const bplg_arch *arch, int32_t method, int32_t budget,
+                         uint64_t seed, bplg_cost_fn cost, void *user, int32_t *chosen,
+                         bplg_tune_report *report);
+
+/* The plan for (op, dtype, n, batch) without any GPU evaluation ("online"
+ * tuning, Section IV): the plan cached by an earlier bplg_tune_plan, else the
+ * analytical guideline on the current device.
+ * Errors: INVALID_ARG, UNSUPPORTED_SIZE, CUDA, NO_DEVICE. */
+int bplg_query_plan(int32_t op, int32_t dtype, int64_t n, int64_t batch, bplg_plan *out);
+
+/* Median time in milliseconds of `reps` launches of `plan` (after two
+ * warm-up launches) on library-owned buffers of shape (dtype, n, batch),
+ * each launch bracketed by CUDA events: the objective f(a_j, x_B) the tuners
+ * minimise.  Allocates and frees its buffers; synchronous.
+ * Errors: INVALID_ARG, INVALID_PLAN, CUDA. */
+int bplg_time_plan(const bplg_plan *plan, int32_t dtype, int64_t n, int64_t batch, int32_t reps,
+                   double *median_ms);
+
+/* Validate `plan` for (op, dtype, n) on the current device.
+ * Returns BPLG_OK or BPLG_ERR_INVALID_PLAN (reason in bplg_last_error()). */
+int bplg_check_plan(const bplg_plan *plan, int32_t dtype, int64_t n);
+
+/* Message of the last error on the calling thread ("" if none). */
+const char *bplg_last_error(void);
+
+/* ABI version (major * 100 + minor). */
+int32_t bplg_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* BPLG_H */

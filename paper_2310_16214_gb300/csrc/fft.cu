@@ -1,0 +1,435 @@
+// Batched complex Stockham FFT (Section III, "Fast Fourier Transform",
+// Fig. 1(c); knobs of Section V-C).
+//
+// A block holds `spb` signals of n = 2^logn points; each signal is served by
+// T = n/R threads and every thread computes one radix-R butterfly per stage
+// (P = r, as in the paper).  Stage s (stride Ns = product of the earlier
+// radices) reads x[j + m T], m = 0..R-1, multiplies element m by W_{Ns R}^{m k}
+// with k = j mod Ns, runs an R-point DFT in registers and writes element r to
+// (j div Ns) Ns R + k + r Ns -- the self-sorting Stockham index map, so the
+// result comes out in natural order with no bit reversal.  When log2 R does
+// not divide logn the first stage uses the lower radix 2^(logn mod log2 R)
+// (the mixed-radix technique of Section VI-A), each thread then doing R/R0
+// butterflies.  Stages exchange data through shared memory:
+//   smem_layout 0  interleaved complex, one float2 per element;
+//   smem_layout 1  real parts then imaginary parts through one float buffer
+//                  (the exchange multiplexing of Section V-C: half the space);
+//   smem_pad       one pad slot per 16 (float2) or 32 (float) elements, which
+//                  makes the strided Stockham writes conflict-free;
+//   io 0 / 1       first and last stage talk to global memory directly
+//                  (8-byte coalesced), or the whole tile is staged through
+//                  shared memory with 16-byte accesses.
+// Twiddles W_M^k = exp(-2 pi i k / M) are generated once per device in float64
+// (sincospi) and rounded to float32; the inverse uses their conjugates.
+#include <mutex>
+#include <unordered_map>
+
+#include "device_util.cuh"
+#include "internal.h"
+
+namespace bplg {
+
+// cos and sin of 2 pi k / 16, k = 0..4 (the other eighths follow by symmetry)
+__host__ __device__ constexpr float cos16(int k) {
+    switch (k & 15) {
+        case 0: return 1.0f;
+        case 1: return 0.92387953251128675613f;
+        case 2: return 0.70710678118654752440f;
+        case 3: return 0.38268343236508977173f;
+        case 4: return 0.0f;
+        case 5: return -0.38268343236508977173f;
+        case 6: return -0.70710678118654752440f;
+        case 7: return -0.92387953251128675613f;
+        case 8: return -1.0f;
+        case 9: return -0.92387953251128675613f;
+        case 10: return -0.70710678118654752440f;
+        case 11: return -0.38268343236508977173f;
+        case 12: return 0.0f;
+        case 13: return 0.38268343236508977173f;
+        case 14: return 0.70710678118654752440f;
+        default: return 0.92387953251128675613f;
+    }
+}
+__host__ __device__ constexpr float sin16(int k) { return cos16(k - 4); }
+
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ float2 cmul(float2 a, float2 w) {
+    return make_float2(a.x * w.x - a.y * w.y, a.x * w.y + a.y * w.x);
+}
+
+// a * exp(DIR 2 pi i k / m) for compile-time k, m in {2, 4, 8, 16}
+template <int DIR, int K, int M>
+__device__ __forceinline__ float2 cmul_root(float2 a) {
+    constexpr int k16 = (K * (16 / M)) & 15;
+    if constexpr (k16 == 0) {
+        return a;
+    } else if constexpr (k16 == 8) {
+        return make_float2(-a.x, -a.y);
+    } else if constexpr (k16 == 4) {  // w = DIR * i
+        return DIR < 0 ? make_float2(a.y, -a.x) : make_float2(-a.y, a.x);
+    } else if constexpr (k16 == 12) {  // w = -DIR * i
+        return DIR < 0 ? make_float2(-a.y, a.x) : make_float2(a.y, -a.x);
+    } else {
+        constexpr float c = cos16(k16);
+        constexpr float s = DIR * sin16(k16);
+        return make_float2(a.x * c - a.y * s, a.x * s + a.y * c);
+    }
+}
+
+__host__ __device__ constexpr int bitrev(int i, int bits) {
+    int r = 0;
+    for (int b = 0; b < bits; ++b) r |= ((i >> b) & 1) << (bits - 1 - b);
+    return r;
+}
+__host__ __device__ constexpr int clog2(int v) { return v <= 1 ? 0 : 1 + clog2(v / 2); }
+
+// One radix-2 decimation-in-frequency layer of half-size H on R registers:
+// (a, b) -> (a + b, (a - b) W_{2H}^k).
+template <int R, int DIR, int H, int B0, int K>
+__device__ __forceinline__ void dif_bfly(float2 (&v)[R]) {
+    if constexpr (B0 < R) {
+        if constexpr (K < H) {
+            float2 a = v[B0 + K], b = v[B0 + K + H];
+            v[B0 + K] = cadd(a, b);
+            v[B0 + K + H] = cmul_root<DIR, K, 2 * H>(csub(a, b));
+            dif_bfly<R, DIR, H, B0, K + 1>(v);
+        } else {
+            dif_bfly<R, DIR, H, B0 + 2 * H, 0>(v);
+        }
+    }
+}
+template <int R, int DIR, int H>
+__device__ __forceinline__ void dif_layers(float2 (&v)[R]) {
+    if constexpr (H >= 1) {
+        dif_bfly<R, DIR, H, 0, 0>(v);
+        dif_layers<R, DIR, H / 2>(v);
+    }
+}
+
+// In-register R-point DFT, natural order in and out.
+template <int R, int DIR>
+__device__ __forceinline__ void dft_codelet(float2 (&v)[R]) {
+    if constexpr (R > 1) {
+        dif_layers<R, DIR, R / 2>(v);
+        float2 t[R];
+#pragma unroll
+        for (int i = 0; i < R; ++i) t[i] = v[bitrev(i, clog2(R))];
+#pragma unroll
+        for (int i = 0; i < R; ++i) v[i] = t[i];
+    }
+}
+
+// First stage with the lower radix R0 (Ns = 1, no twiddles): the thread's R
+// registers hold R/R0 butterflies, butterfly q using registers q, q+Q, ...
+template <int R, int R0, int DIR>
+__device__ __forceinline__ void first_stage_mixed(float2 (&v)[R]) {
+    constexpr int Q = R / R0;
+#pragma unroll
+    for (int q = 0; q < Q; ++q) {
+        float2 u[R0];
+#pragma unroll
+        for (int r = 0; r < R0; ++r) u[r] = v[q + r * Q];
+        dft_codelet<R0, DIR>(u);
+#pragma unroll
+        for (int r = 0; r < R0; ++r) v[q + r * Q] = u[r];
+    }
+}
+
+// Output position of register m after a stage.  Radix-R stage: base + m Ns.
+// Mixed first stage of radix R0 = 2^lr0 (Q = R / R0 butterflies per thread):
+// register m = q + r Q holds output r of butterfly j + q T, i.e. position
+// (j + q T) R0 + r.
+struct OutMap {
+    int base, shift, mixed, lr0, lq, j, T;
+    __device__ __forceinline__ int operator()(int m) const {
+        if (mixed) return ((j + (m & ((1 << lq) - 1)) * T) << lr0) + (m >> lq);
+        return base + (m << shift);
+    }
+};
+
+template <int LAYOUT, int PAD>
+__device__ __forceinline__ int pidx(int e) {
+    if constexpr (!PAD) return e;
+    if constexpr (LAYOUT == 0) return e + (e >> 4);
+    return e + (e >> 5);
+}
+
+template <int LAYOUT, int PAD>
+__host__ __device__ __forceinline__ int sig_stride(int n) {
+    if (!PAD) return n;
+    int p = LAYOUT == 0 ? (n >> 4) : (n >> 5);
+    return n + (p > 0 ? p : 1);
+}
+
+template <int R, int DIR, int LAYOUT, int PAD, int STAGED, int MAXT>
+__global__ void __launch_bounds__(MAXT)
+    fft_kernel(const float2 *in, float2 *out, const float2 *__restrict__ tw, int logn, int spb,
+               int64_t batch) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    constexpr int LR = clog2(R);
+    const int n = 1 << logn;
+    const int logT = logn - LR;
+    const int T = 1 << logT;
+    const int tid = threadIdx.x;
+    const int s = tid >> logT;
+    const int j = tid & (T - 1);
+    const int64_t sig0 = static_cast<int64_t>(blockIdx.x) * spb;
+    const int64_t sig = sig0 + s;
+    const bool active = sig < batch;
+    const int64_t left = batch - sig0;
+    const int nvalid = left < spb ? static_cast<int>(left) : spb;
+    const int stride = sig_stride<LAYOUT, PAD>(n);
+    float2 *buf2 = reinterpret_cast<float2 *>(smem_raw);
+    float *buf1 = reinterpret_cast<float *>(smem_raw);
+    const int sbase = s * stride;
+
+    float2 v[R];
+    OutMap om{0, 0, 0, 0, 0, j, T};
+    if constexpr (STAGED) {
+        const float4 *g = reinterpret_cast<const float4 *>(in + sig0 * n);
+        const int count4 = (nvalid * n) >> 1;
+        for (int q = tid; q < count4; q += blockDim.x) {
+            float4 w = __ldcs(g + q);
+            const int e0 = q << 1;
+            const int ss = e0 >> logn;
+            const int e = e0 & (n - 1);
+            buf2[ss * stride + pidx<0, PAD>(e)] = make_float2(w.x, w.y);
+            buf2[ss * stride + pidx<0, PAD>(e + 1)] = make_float2(w.z, w.w);
+        }
+        __syncthreads();
+#pragma unroll
+        for (int m = 0; m < R; ++m) v[m] = buf2[sbase + pidx<0, PAD>(j + m * T)];
+    } else {
+        const float2 *g = in + sig * n + j;
+#pragma unroll
+        for (int m = 0; m < R; ++m) v[m] = active ? __ldcs(g + m * T) : make_float2(0.f, 0.f);
+    }
+
+    const int lr0 = logn % LR;
+    const int nstages = (lr0 ? 1 : 0) + logn / LR;
+    int logNs = 0;
+    for (int st = 0; st < nstages; ++st) {
+        if (st == 0 && lr0 != 0) {
+            if constexpr (R >= 4) {
+                if (lr0 == 1) first_stage_mixed<R, 2, DIR>(v);
+            }
+            if constexpr (R >= 8) {
+                if (lr0 == 2) first_stage_mixed<R, 4, DIR>(v);
+            }
+            if constexpr (R >= 16) {
+                if (lr0 == 3) first_stage_mixed<R, 8, DIR>(v);
+            }
+            om.mixed = 1;
+            om.lr0 = lr0;
+            om.lq = LR - lr0;
+            logNs = lr0;
+        } else {
+            const int Ns = 1 << logNs;
+            const int k = j & (Ns - 1);
+            if (logNs > 0) {
+                const float2 *twp = tw + (Ns << LR);
+#pragma unroll
+                for (int r = 1; r < R; ++r) {
+                    float2 w = __ldg(twp + r * k);
+                    if (DIR > 0) w.y = -w.y;
+                    v[r] = cmul(v[r], w);
+                }
+            }
+            dft_codelet<R, DIR>(v);
+            om.mixed = 0;
+            om.base = ((j >> logNs) << (logNs + LR)) + k;
+            om.shift = logNs;
+            logNs += LR;
+        }
+        if (st == nstages - 1) break;
+        // exchange through shared memory for the next stage
+        if constexpr (LAYOUT == 0) {
+            __syncthreads();
+#pragma unroll
+            for (int r = 0; r < R; ++r) buf2[sbase + pidx<0, PAD>(om(r))] = v[r];
+            __syncthreads();
+#pragma unroll
+            for (int m = 0; m < R; ++m) v[m] = buf2[sbase + pidx<0, PAD>(j + m * T)];
+        } else {
+            __syncthreads();
+#pragma unroll
+            for (int r = 0; r < R; ++r) buf1[sbase + pidx<1, PAD>(om(r))] = v[r].x;
+            __syncthreads();
+#pragma unroll
+            for (int m = 0; m < R; ++m) v[m].x = buf1[sbase + pidx<1, PAD>(j + m * T)];
+            __syncthreads();
+#pragma unroll
+            for (int r = 0; r < R; ++r) buf1[sbase + pidx<1, PAD>(om(r))] = v[r].y;
+            __syncthreads();
+#pragma unroll
+            for (int m = 0; m < R; ++m) v[m].y = buf1[sbase + pidx<1, PAD>(j + m * T)];
+        }
+    }
+
+    if constexpr (STAGED) {
+        __syncthreads();
+#pragma unroll
+        for (int r = 0; r < R; ++r) buf2[sbase + pidx<0, PAD>(om(r))] = v[r];
+        __syncthreads();
+        float4 *g = reinterpret_cast<float4 *>(out + sig0 * n);
+        const int count4 = (nvalid * n) >> 1;
+        for (int q = tid; q < count4; q += blockDim.x) {
+            const int e0 = q << 1;
+            const int ss = e0 >> logn;
+            const int e = e0 & (n - 1);
+            float2 lo = buf2[ss * stride + pidx<0, PAD>(e)];
+            float2 hi = buf2[ss * stride + pidx<0, PAD>(e + 1)];
+            __stcs(g + q, make_float4(lo.x, lo.y, hi.x, hi.y));
+        }
+    } else {
+        if (active) {
+            float2 *g = out + sig * n;
+#pragma unroll
+            for (int r = 0; r < R; ++r) __stcs(g + om(r), v[r]);
+        }
+    }
+}
+
+// Twiddle table: tw[M + k] = exp(-2 pi i k / M) for M = 2, 4, ..., 2^max_log,
+// computed in float64 and rounded once to float32.
+__global__ void twiddle_init_kernel(float2 *tw, int max_log) {
+    const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+    const int64_t total = int64_t(2) << max_log;
+    if (i >= total) return;
+    if (i < 2) {
+        tw[i] = make_float2(1.f, 0.f);
+        return;
+    }
+    const int lm = 63 - __clzll(static_cast<unsigned long long>(i));
+    const int64_t M = int64_t(1) << lm;
+    const int64_t k = i - M;
+    double sn, cs;
+    sincospi(-2.0 * static_cast<double>(k) / static_cast<double>(M), &sn, &cs);
+    tw[i] = make_float2(static_cast<float>(cs), static_cast<float>(sn));
+}
+
+namespace {
+
+// Radix-16 butterflies need more than the 64 registers a 1024-thread block
+// leaves per thread; blocks of at most 512 threads use an instantiation
+// bounded to 512 threads (up to 128 registers).
+template <int R, int DIR, int LAYOUT, int PAD, int MAXT>
+const void *fft_func_io_t(int io) {
+    if constexpr (LAYOUT == 1) {
+        return io == 0 ? reinterpret_cast<const void *>(&fft_kernel<R, DIR, 1, PAD, 0, MAXT>) : nullptr;
+    } else {
+        return io == 0 ? reinterpret_cast<const void *>(&fft_kernel<R, DIR, 0, PAD, 0, MAXT>)
+                       : reinterpret_cast<const void *>(&fft_kernel<R, DIR, 0, PAD, 1, MAXT>);
+    }
+}
+
+template <int R, int DIR, int LAYOUT, int PAD>
+const void *fft_func_io(int io, int threads) {
+    if constexpr (R == 16) {
+        if (threads <= 512) return fft_func_io_t<R, DIR, LAYOUT, PAD, 512>(io);
+    }
+    return fft_func_io_t<R, DIR, LAYOUT, PAD, 1024>(io);
+}
+
+template <int R, int DIR>
+const void *fft_func_rd(int layout, int pad, int io, int threads) {
+    if (layout == 0) return pad ? fft_func_io<R, DIR, 0, 1>(io, threads) : fft_func_io<R, DIR, 0, 0>(io, threads);
+    return pad ? fft_func_io<R, DIR, 1, 1>(io, threads) : fft_func_io<R, DIR, 1, 0>(io, threads);
+}
+
+template <int DIR>
+const void *fft_func_d(int radix, int layout, int pad, int io, int threads) {
+    switch (radix) {
+        case 2: return fft_func_rd<2, DIR>(layout, pad, io, threads);
+        case 4: return fft_func_rd<4, DIR>(layout, pad, io, threads);
+        case 8: return fft_func_rd<8, DIR>(layout, pad, io, threads);
+        case 16: return fft_func_rd<16, DIR>(layout, pad, io, threads);
+        default: return nullptr;
+    }
+}
+
+const void *fft_func(int radix, int dir, int layout, int pad, int io, int threads) {
+    if (layout < 0 || layout > 1 || pad < 0 || pad > 1 || io < 0 || io > 1) return nullptr;
+    return dir < 0 ? fft_func_d<-1>(radix, layout, pad, io, threads)
+                   : fft_func_d<1>(radix, layout, pad, io, threads);
+}
+
+std::mutex g_tw_mu;
+std::unordered_map<int, float2 *> g_tw;
+
+}  // namespace
+
+int fft_smem_bytes(int radix, int layout, int pad, int io, int64_t n, int spb) {
+    const int logn = ilog2(n);
+    const int lr = ilog2(radix);
+    const int nstages = (logn % lr ? 1 : 0) + logn / lr;
+    if (nstages <= 1 && io == 0) return 0;
+    const int stride = layout == 0 ? (pad ? sig_stride<0, 1>(static_cast<int>(n)) : static_cast<int>(n))
+                                   : (pad ? sig_stride<1, 1>(static_cast<int>(n)) : static_cast<int>(n));
+    return spb * stride * (layout == 0 ? 8 : 4);
+}
+
+int twiddles_for_current_device(const void **tw) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_error(e, "cudaGetDevice");
+    std::lock_guard<std::mutex> lock(g_tw_mu);
+    auto it = g_tw.find(dev);
+    if (it != g_tw.end()) {
+        *tw = it->second;
+        return BPLG_OK;
+    }
+    const int64_t total = int64_t(2) << kFftMaxLog;
+    float2 *p = nullptr;
+    e = cudaMalloc(&p, total * sizeof(float2));
+    if (e != cudaSuccess) return cuda_error(e, "twiddle table cudaMalloc");
+    cudaStream_t st;
+    e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+        cudaFree(p);
+        return cuda_error(e, "twiddle stream");
+    }
+    twiddle_init_kernel<<<static_cast<unsigned>((total + 255) / 256), 256, 0, st>>>(p, kFftMaxLog);
+    e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    cudaStreamDestroy(st);
+    if (e != cudaSuccess) {
+        cudaFree(p);
+        return cuda_error(e, "twiddle generation");
+    }
+    g_tw[dev] = p;
+    *tw = p;
+    return BPLG_OK;
+}
+
+bool fft_launch_info(const bplg_plan &p, int64_t n, int64_t batch, int dir, Launch *out) {
+    std::string why;
+    if (!plan_structurally_valid(p, BPLG_F32, n, &why)) return false;
+    const void *f = fft_func(p.radix, dir, p.smem_layout, p.smem_pad, p.io, p.L);
+    if (!f) return false;
+    out->func = f;
+    out->threads = p.L;
+    out->smem = fft_smem_bytes(p.radix, p.smem_layout, p.smem_pad, p.io, n, p.spb);
+    out->blocks = (batch + p.spb - 1) / p.spb;
+    return true;
+}
+
+int fft_launch(const bplg_plan &p, const void *in, void *out, int64_t n, int64_t batch, int dir,
+               cudaStream_t s) {
+    Launch li;
+    if (!fft_launch_info(p, n, batch, dir, &li)) return set_error(BPLG_ERR_INVALID_PLAN, "fft: plan has no kernel");
+    const void *tw = nullptr;
+    int rc = twiddles_for_current_device(&tw);
+    if (rc != BPLG_OK) return rc;
+    rc = ensure_smem_attr(li.func, li.smem);
+    if (rc != BPLG_OK) return rc;
+    int logn = ilog2(n);
+    int spb = p.spb;
+    void *args[] = {(void *)&in, (void *)&out, (void *)&tw, &logn, &spb, &batch};
+    cudaError_t e = cudaLaunchKernel(li.func, dim3(static_cast<unsigned>(li.blocks)), dim3(li.threads), args,
+                                     static_cast<size_t>(li.smem), s);
+    return e == cudaSuccess ? BPLG_OK : cuda_error(e, "fft launch");
+}
+
+}  // namespace bplg

@@ -1,0 +1,80 @@
+// Host-side internals shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "bplg.h"
+
+namespace bplg {
+
+// thread-local last-error message; returns `code` for convenient tail calls
+int set_error(int code, const std::string &msg);
+int cuda_error(cudaError_t e, const char *what);
+void clear_error();
+
+inline bool is_pow2(int64_t v) { return v > 0 && (v & (v - 1)) == 0; }
+inline int ilog2(int64_t v) {
+    int l = 0;
+    while ((int64_t(1) << (l + 1)) <= v) ++l;
+    return l;
+}
+inline bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
+// Kernel function pointer plus the launch geometry derived from a plan.
+struct Launch {
+    const void *func = nullptr;  // __global__ function (for attributes)
+    int threads = 0;             // threads per block
+    int smem = 0;                // dynamic shared memory bytes
+    int64_t blocks = 0;          // grid size
+};
+
+// Largest sizes each family supports.
+constexpr int kScanMaxLog = 15;
+constexpr int kFftMaxLog = 14;
+constexpr int kTridiagMaxLog = 13;
+constexpr int kRefinedMaxLog = 12;
+
+// ---- per-op kernel tables (each returns false if the plan has no kernel)
+bool scan_launch_info(const bplg_plan &p, int dtype, int64_t n, int64_t batch, Launch *out);
+int scan_launch(const bplg_plan &p, int dtype, const void *in, void *out, int64_t n, int64_t batch,
+                cudaStream_t s);
+
+bool fft_launch_info(const bplg_plan &p, int64_t n, int64_t batch, int dir, Launch *out);
+int fft_launch(const bplg_plan &p, const void *in, void *out, int64_t n, int64_t batch, int dir,
+               cudaStream_t s);
+
+bool tridiag_launch_info(const bplg_plan &p, int64_t n, int64_t batch, bool refined, Launch *out);
+int tridiag_launch(const bplg_plan &p, const float *a, const float *b, const float *c,
+                   const float *d, float *x, int64_t n, int64_t batch, cudaStream_t s);
+int tridiag_refined_launch(const bplg_plan &p, const float *a, const float *b, const float *c,
+                           const float *d, double *x, int64_t n, int64_t batch, int max_iter,
+                           double tol, int32_t *iters, cudaStream_t s);
+
+// ---- plans
+// structural validity (sizes, knob ranges, geometry); no device query
+bool plan_structurally_valid(const bplg_plan &p, int dtype, int64_t n, std::string *why);
+// structural validity + device limits (threads, shared memory, registers)
+int check_plan_on_device(const bplg_plan &p, int dtype, int64_t n, std::string *why);
+// canonical enumeration of the structurally valid plans
+std::vector<bplg_plan> enumerate_structural(int op, int dtype, int64_t n);
+// shared memory (dynamic) a plan needs, in bytes
+int plan_smem_bytes(const bplg_plan &p, int dtype, int64_t n);
+// make S consistent with the other knobs
+void plan_finalize(bplg_plan *p, int dtype, int64_t n);
+
+// raise the dynamic shared-memory limit of `func` once per device
+int ensure_smem_attr(const void *func, int smem);
+
+// ---- plan cache (per process) and defaults
+bool cache_lookup(int op, int dtype, int64_t n, int64_t batch, bplg_plan *out);
+void cache_store(int op, int dtype, int64_t n, int64_t batch, const bplg_plan &p);
+int analytic_plan(int op, int dtype, int64_t n, bplg_plan *out);
+
+// twiddle table of the current device (float2 W_M^k at [M + k], M = 2..2^14)
+int twiddles_for_current_device(const void **tw);
+
+}  // namespace bplg

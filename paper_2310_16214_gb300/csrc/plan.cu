@@ -1,0 +1,319 @@
+// Plans: validity of a knob tuple for a problem size, canonical enumeration
+// of the search space (Section IV-B, Table I; constraints of Section V
+// restated for the GB300), shared-memory sizes, the per-process plan cache,
+// and the per-device dynamic shared-memory opt-in.
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <fstream>
+#include <map>
+#include <mutex>
+#include <set>
+#include <sstream>
+#include <tuple>
+
+#include "internal.h"
+
+namespace bplg {
+
+int fft_smem_bytes(int radix, int layout, int pad, int io, int64_t n, int spb);
+int tridiag_smem_bytes(int pad, int64_t n, int spb, bool refined);
+
+namespace {
+thread_local std::string t_last_error;
+}
+
+int set_error(int code, const std::string &msg) {
+    t_last_error = msg;
+    return code;
+}
+
+int cuda_error(cudaError_t e, const char *what) {
+    std::string m = std::string(what) + ": " + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) + ")";
+    t_last_error = m;
+    if (e == cudaErrorNoDevice || e == cudaErrorInsufficientDriver) return BPLG_ERR_NO_DEVICE;
+    return BPLG_ERR_CUDA;
+}
+
+void clear_error() { t_last_error.clear(); }
+
+const char *last_error_cstr() { return t_last_error.c_str(); }
+
+static bool fail(std::string *why, const char *msg) {
+    if (why) *why = msg;
+    return false;
+}
+
+int max_log_for(int op) {
+    switch (op) {
+        case BPLG_OP_SCAN: return kScanMaxLog;
+        case BPLG_OP_FFT: return kFftMaxLog;
+        case BPLG_OP_TRIDIAG: return kTridiagMaxLog;
+        case BPLG_OP_TRIDIAG_REFINED: return kRefinedMaxLog;
+        default: return -1;
+    }
+}
+
+bool plan_structurally_valid(const bplg_plan &p, int dtype, int64_t n, std::string *why) {
+    const int ml = max_log_for(p.op);
+    if (ml < 0) return fail(why, "unknown op");
+    if (!is_pow2(n) || n > (int64_t(1) << ml)) return fail(why, "n is not a supported power of two");
+    if (p.n != 0 && p.n != n) return fail(why, "plan was made for another n");
+    if (!is_pow2(p.P) || p.P > 32 || p.P > n) return fail(why, "P must be a power of two <= min(32, n)");
+    if (p.spb < 1) return fail(why, "spb must be >= 1");
+    const int64_t tps = n / p.P;
+    if (tps > 1024) return fail(why, "more than 1024 threads per problem");
+    if (int64_t(p.spb) * tps != p.L) return fail(why, "L must equal spb * n / P");
+    if (p.L < 32 || p.L > 1024 || (p.L & 31)) return fail(why, "L must be a multiple of 32 in [32, 1024]");
+    switch (p.op) {
+        case BPLG_OP_SCAN:
+            if (dtype != BPLG_I32 && dtype != BPLG_F32) return fail(why, "scan dtype must be I32 or F32");
+            if (p.pattern != BPLG_PATTERN_KS && p.pattern != BPLG_PATTERN_LF) return fail(why, "bad scan pattern");
+            if (tps > 32 * 32) return fail(why, "scan: at most 32 warps per problem");
+            return true;
+        case BPLG_OP_FFT:
+            if (p.radix != 2 && p.radix != 4 && p.radix != 8 && p.radix != 16) return fail(why, "radix must be 2, 4, 8 or 16");
+            if (p.P != p.radix) return fail(why, "FFT: P must equal the radix");
+            if (n < 2) return fail(why, "FFT: n >= 2");
+            if (p.smem_layout < 0 || p.smem_layout > 1 || p.smem_pad < 0 || p.smem_pad > 1 || p.io < 0 || p.io > 1)
+                return fail(why, "FFT: layout/pad/io out of range");
+            if (p.smem_layout == 1 && p.io == 1) return fail(why, "FFT: staged io needs the interleaved layout");
+            return true;
+        case BPLG_OP_TRIDIAG:
+        case BPLG_OP_TRIDIAG_REFINED: {
+            if (n < 2) return fail(why, "tridiag: n >= 2");
+            if (p.P > 16) return fail(why, "tridiag: P <= 16");
+            if (!is_pow2(p.cr_switch) || p.cr_switch > n || p.cr_switch > tps)
+                return fail(why, "tridiag: cr_switch must be a power of two <= min(n, n/P)");
+            if (p.shuffle < 0 || p.shuffle > 1 || p.smem_pad < 0 || p.smem_pad > 1)
+                return fail(why, "tridiag: shuffle/pad out of range");
+            if (p.shuffle && p.cr_switch > 32) return fail(why, "tridiag: shuffle PCR needs cr_switch <= 32");
+            if (p.op == BPLG_OP_TRIDIAG_REFINED && tps < 32) return fail(why, "refined: at least 32 threads per system");
+            return true;
+        }
+        default:
+            return fail(why, "unknown op");
+    }
+}
+
+int plan_smem_bytes(const bplg_plan &p, int dtype, int64_t n) {
+    (void)dtype;
+    switch (p.op) {
+        case BPLG_OP_SCAN: return 0;
+        case BPLG_OP_FFT: return fft_smem_bytes(p.radix, p.smem_layout, p.smem_pad, p.io, n, p.spb);
+        case BPLG_OP_TRIDIAG: return tridiag_smem_bytes(p.smem_pad, n, p.spb, false);
+        case BPLG_OP_TRIDIAG_REFINED: return tridiag_smem_bytes(p.smem_pad, n, p.spb, true);
+        default: return 0;
+    }
+}
+
+void plan_finalize(bplg_plan *p, int dtype, int64_t n) {
+    p->n = static_cast<int32_t>(n);
+    const int64_t tps = p->P > 0 ? n / p->P : 0;
+    p->L = static_cast<int32_t>(p->spb * tps);
+    switch (p->op) {
+        case BPLG_OP_SCAN:
+            p->radix = 2;
+            p->shuffle = 1;
+            p->smem_layout = p->smem_pad = p->io = p->cr_switch = 0;
+            p->S = tps > 32 ? p->L / 32 : 0;
+            break;
+        case BPLG_OP_FFT:
+            p->radix = p->P;
+            p->shuffle = 0;
+            p->pattern = p->cr_switch = 0;
+            p->S = plan_smem_bytes(*p, dtype, n) > 0 ? static_cast<int32_t>(p->spb * n) : 0;
+            break;
+        case BPLG_OP_TRIDIAG:
+        case BPLG_OP_TRIDIAG_REFINED:
+            p->radix = 2;
+            p->pattern = p->smem_layout = p->io = 0;
+            p->S = static_cast<int32_t>(p->spb * n);
+            break;
+        default:
+            break;
+    }
+    std::memset(p->reserved, 0, sizeof(p->reserved));
+}
+
+std::vector<bplg_plan> enumerate_structural(int op, int dtype, int64_t n) {
+    std::vector<bplg_plan> out;
+    if (max_log_for(op) < 0 || !is_pow2(n) || n > (int64_t(1) << max_log_for(op))) return out;
+    auto push = [&](bplg_plan p) {
+        plan_finalize(&p, dtype, n);
+        if (plan_structurally_valid(p, dtype, n, nullptr)) out.push_back(p);
+    };
+    for (int P = 1; P <= 32; P *= 2) {
+        if (P > n) break;
+        const int64_t tps = n / P;
+        if (tps > 1024) continue;
+        for (int L = 32; L <= 1024; L *= 2) {
+            if (L < tps || L % tps) continue;
+            const int spb = static_cast<int>(L / tps);
+            bplg_plan p;
+            std::memset(&p, 0, sizeof(p));
+            p.op = op;
+            p.P = P;
+            p.spb = spb;
+            if (op == BPLG_OP_SCAN) {
+                for (int pat = 0; pat <= 1; ++pat) {
+                    p.pattern = pat;
+                    push(p);
+                }
+            } else if (op == BPLG_OP_FFT) {
+                if (P < 2 || P > 16) continue;
+                p.radix = P;
+                const int io_first = tps >= 32 ? 0 : 1;
+                for (int io_i = 0; io_i < 2; ++io_i) {
+                    const int io = io_i == 0 ? io_first : 1 - io_first;
+                    for (int layout = 0; layout <= 1; ++layout) {
+                        for (int pad = 1; pad >= 0; --pad) {
+                            p.io = io;
+                            p.smem_layout = layout;
+                            p.smem_pad = pad;
+                            push(p);
+                        }
+                    }
+                }
+            } else {
+                const int64_t mmax = tps < n ? tps : n;
+                for (int64_t m = mmax; m >= 1; m /= 2) {
+                    for (int sh = 1; sh >= 0; --sh) {
+                        for (int pad = 1; pad >= 0; --pad) {
+                            p.cr_switch = static_cast<int32_t>(m);
+                            p.shuffle = sh;
+                            p.smem_pad = pad;
+                            push(p);
+                        }
+                    }
+                }
+            }
+        }
+    }
+    return out;
+}
+
+// ------------------------------------------------------------ smem attribute
+namespace {
+std::mutex g_attr_mu;
+std::map<std::pair<int, const void *>, int> g_attr;  // (device, func) -> max dynamic smem set
+}  // namespace
+
+int ensure_smem_attr(const void *func, int smem) {
+    if (smem <= 48 * 1024) return BPLG_OK;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_error(e, "cudaGetDevice");
+    std::lock_guard<std::mutex> lock(g_attr_mu);
+    auto key = std::make_pair(dev, func);
+    auto it = g_attr.find(key);
+    if (it != g_attr.end() && it->second >= smem) return BPLG_OK;
+    e = cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return cuda_error(e, "cudaFuncSetAttribute(max dynamic smem)");
+    g_attr[key] = smem;
+    return BPLG_OK;
+}
+
+bool launch_info_for(const bplg_plan &p, int dtype, int64_t n, Launch *li) {
+    switch (p.op) {
+        case BPLG_OP_SCAN: return scan_launch_info(p, dtype, n, 1, li);
+        case BPLG_OP_FFT: return fft_launch_info(p, n, 1, -1, li);
+        case BPLG_OP_TRIDIAG: return tridiag_launch_info(p, n, 1, false, li);
+        case BPLG_OP_TRIDIAG_REFINED: return tridiag_launch_info(p, n, 1, true, li);
+        default: return false;
+    }
+}
+
+int check_plan_on_device(const bplg_plan &p, int dtype, int64_t n, std::string *why) {
+    if (!plan_structurally_valid(p, dtype, n, why)) return BPLG_ERR_INVALID_PLAN;
+    Launch li;
+    if (!launch_info_for(p, dtype, n, &li)) {
+        if (why) *why = "no kernel for this knob tuple";
+        return BPLG_ERR_INVALID_PLAN;
+    }
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_error(e, "cudaGetDevice");
+    cudaFuncAttributes fa;
+    e = cudaFuncGetAttributes(&fa, li.func);
+    if (e != cudaSuccess) return cuda_error(e, "cudaFuncGetAttributes");
+    int optin = 0;
+    e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (e != cudaSuccess) return cuda_error(e, "cudaDeviceGetAttribute");
+    if (li.threads > fa.maxThreadsPerBlock) {
+        if (why) *why = "block larger than the kernel's thread limit";
+        return BPLG_ERR_INVALID_PLAN;
+    }
+    if (static_cast<int64_t>(li.smem) + static_cast<int64_t>(fa.sharedSizeBytes) > optin) {
+        if (why) *why = "shared memory above the per-block limit";
+        return BPLG_ERR_INVALID_PLAN;
+    }
+    return BPLG_OK;
+}
+
+// ------------------------------------------------------------- plan cache
+namespace {
+std::mutex g_cache_mu;
+std::map<std::tuple<int, int, int64_t, int>, bplg_plan> g_cache;
+bool g_cache_loaded = false;
+
+int batch_class(int64_t batch) { return ilog2(batch < 1 ? 1 : batch); }
+
+const char *cache_file() {
+    const char *f = std::getenv("BPLG_PLAN_CACHE");
+    return (f && *f) ? f : nullptr;
+}
+
+void load_cache_locked() {
+    if (g_cache_loaded) return;
+    g_cache_loaded = true;
+    const char *f = cache_file();
+    if (!f) return;
+    std::ifstream in(f);
+    std::string line;
+    while (std::getline(in, line)) {
+        if (line.empty() || line[0] == '#') continue;
+        std::istringstream ss(line);
+        int op, dtype, bc;
+        int64_t n;
+        bplg_plan p;
+        std::memset(&p, 0, sizeof(p));
+        if (!(ss >> op >> dtype >> n >> bc >> p.op >> p.n >> p.P >> p.L >> p.spb >> p.S >> p.radix >> p.shuffle >>
+              p.pattern >> p.smem_layout >> p.smem_pad >> p.io >> p.cr_switch))
+            continue;
+        if (plan_structurally_valid(p, dtype, n, nullptr)) g_cache[std::make_tuple(op, dtype, n, bc)] = p;
+    }
+}
+
+void save_cache_locked() {
+    const char *f = cache_file();
+    if (!f) return;
+    std::ofstream out(f, std::ios::trunc);
+    out << "# op dtype n batch_log2 | op n P L spb S radix shuffle pattern layout pad io cr_switch\n";
+    for (const auto &kv : g_cache) {
+        const bplg_plan &p = kv.second;
+        out << std::get<0>(kv.first) << ' ' << std::get<1>(kv.first) << ' ' << std::get<2>(kv.first) << ' '
+            << std::get<3>(kv.first) << ' ' << p.op << ' ' << p.n << ' ' << p.P << ' ' << p.L << ' ' << p.spb << ' '
+            << p.S << ' ' << p.radix << ' ' << p.shuffle << ' ' << p.pattern << ' ' << p.smem_layout << ' '
+            << p.smem_pad << ' ' << p.io << ' ' << p.cr_switch << '\n';
+    }
+}
+}  // namespace
+
+bool cache_lookup(int op, int dtype, int64_t n, int64_t batch, bplg_plan *out) {
+    std::lock_guard<std::mutex> lock(g_cache_mu);
+    load_cache_locked();
+    auto it = g_cache.find(std::make_tuple(op, dtype, n, batch_class(batch)));
+    if (it == g_cache.end()) return false;
+    *out = it->second;
+    return true;
+}
+
+void cache_store(int op, int dtype, int64_t n, int64_t batch, const bplg_plan &p) {
+    std::lock_guard<std::mutex> lock(g_cache_mu);
+    load_cache_locked();
+    g_cache[std::make_tuple(op, dtype, n, batch_class(batch))] = p;
+    save_cache_locked();
+}
+
+}  // namespace bplg

@@ -1,0 +1,135 @@
+"""Tridiagonal CR/PCR parity on the GPU against the float64 Thomas oracle on
+the stored float32 systems: relative error <= 1e-4 per system for the float32
+solver over every valid plan (threads per system, systems per block,
+cr_switch, shuffle PCR, padding) with a ragged batch; <= 1e-12 after the
+float64-residual refinement."""
+import numpy as np
+import pytest
+
+import oracle
+import seeded_inputs as si
+from tests.gpu_util import sample_rows, to_dev, tri_rel_err
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def bp():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2310_16214_gb300 as bp
+    return bp
+
+
+def run_tri(bp, sysm, plan=None):
+    a, b, c, d = sysm[:4]
+    batch, n = b.shape
+    ts = [to_dev(v) for v in (a, b, c, d)]
+    x = torch.empty_like(ts[0])
+    bp.tridiag_batched(*ts, x, n, batch, plan=plan)
+    torch.cuda.synchronize()
+    return x.cpu().numpy()
+
+
+def run_refined(bp, sysm, plan=None, max_iter=10, tol=1e-14):
+    a, b, c, d = sysm[:4]
+    batch, n = b.shape
+    ts = [to_dev(v) for v in (a, b, c, d)]
+    x = torch.empty((batch, n), dtype=torch.float64, device="cuda")
+    it = torch.zeros(batch, dtype=torch.int32, device="cuda")
+    bp.tridiag_refined(*ts, x, n, batch, max_iter=max_iter, tol=tol, iters=it, plan=plan)
+    torch.cuda.synchronize()
+    return x.cpu().numpy(), it.cpu().numpy()
+
+
+@pytest.mark.parametrize("n", [2, 4, 32, 64, 256, 1024, 2048, 8192])
+def test_every_plan_ragged(bp, n):
+    batch = 11 if n <= 2048 else 3
+    sysm = si.tridiag_f32(batch, n, stream=n)
+    ref = oracle.thomas(*sysm[:4])
+    plans = bp.enumerate_plans(bp.OP_TRIDIAG, bp.F32, n)
+    assert plans
+    for p in plans:
+        assert tri_rel_err(run_tri(bp, sysm, p), ref).max() <= 1e-4, p
+
+
+def test_outside_coefficients_never_read(bp):
+    n, batch = 256, 5
+    a, b, c, d, _ = si.tridiag_f32(batch, n, stream=3)
+    a[:, 0] = np.nan
+    c[:, -1] = np.nan
+    ref = oracle.thomas(a, b, c, d)
+    x = run_tri(bp, (a, b, c, d))
+    assert np.all(np.isfinite(x)) and tri_rel_err(x, ref).max() <= 1e-4
+
+
+def test_x_may_alias_d(bp):
+    n, batch = 512, 7
+    a, b, c, d, _ = si.tridiag_f32(batch, n, stream=4)
+    ref = oracle.thomas(a, b, c, d)
+    ts = [to_dev(v) for v in (a, b, c, d)]
+    bp.tridiag_batched(*ts, ts[3], n, batch)
+    torch.cuda.synchronize()
+    assert tri_rel_err(ts[3].cpu().numpy(), ref).max() <= 1e-4
+
+
+@pytest.mark.parametrize("n", [64, 256, 1024, 2048])
+def test_full_size_default_plan_sampled(bp, n):
+    batch = (1 << 24) // n
+    sysm = si.tridiag_f32(batch, n, stream=30 + n)
+    x = run_tri(bp, sysm)
+    rows = sample_rows(batch)
+    ref = oracle.thomas(*[v[rows] for v in sysm[:4]])
+    assert tri_rel_err(x[rows], ref).max() <= 1e-4
+
+
+@pytest.mark.parametrize("n", [32, 64, 256, 1024, 4096])
+def test_refined_every_plan(bp, n):
+    batch = 5
+    sysm = si.tridiag_f32(batch, n, stream=50 + n)
+    ref = oracle.thomas(*sysm[:4])
+    for p in bp.enumerate_plans(bp.OP_TRIDIAG_REFINED, bp.F32, n):
+        x, it = run_refined(bp, sysm, p)
+        assert tri_rel_err(x, ref).max() <= 1e-12, p
+        assert np.all(it >= 1) and np.all(it <= 10)
+
+
+def test_refined_full_config_sampled(bp):
+    # n = 1024, 2^14 systems (the precision configuration), default plan
+    n, batch = 1024, 1 << 14
+    sysm = si.tridiag_f32(batch, n, seed=si.CONFIG_SEEDS["precision"])
+    x, it = run_refined(bp, sysm)
+    rows = sample_rows(batch)
+    ref = oracle.thomas(*[v[rows] for v in sysm[:4]])
+    assert tri_rel_err(x[rows], ref).max() <= 1e-12
+    # the float32 solve alone is ~1e-7; refinement must have been applied
+    assert it.min() >= 1
+
+
+def test_refined_zero_iterations_is_the_float32_solve(bp):
+    n, batch = 256, 4
+    sysm = si.tridiag_f32(batch, n, stream=77)
+    ref = oracle.thomas(*sysm[:4])
+    x, it = run_refined(bp, sysm, max_iter=0)
+    assert np.all(it == 0)
+    assert tri_rel_err(x, ref).max() <= 1e-4
+
+
+def test_argument_errors(bp):
+    v = torch.zeros(4096, dtype=torch.float32, device="cuda")
+    with pytest.raises(bp.BplgError) as e:
+        bp.tridiag_batched(v, v, v, v, v, 100, 1)
+    assert e.value.code == bp.ERR_UNSUPPORTED_SIZE
+    x64 = torch.zeros(4096, dtype=torch.float64, device="cuda")
+    with pytest.raises(bp.BplgError) as e:
+        bp.tridiag_refined(v, v, v, v, v, 64, 1)  # x aliases the inputs
+    assert e.value.code == bp.ERR_INVALID_ARG
+    with pytest.raises(bp.BplgError) as e:
+        bp.tridiag_refined(v, v, v, v, x64, 8192, 1)
+    assert e.value.code == bp.ERR_UNSUPPORTED_SIZE
+    bad = bp.make_plan(bp.OP_TRIDIAG, 64, P=2, spb=1, cr_switch=64, shuffle=1)  # shuffle PCR needs m <= 32
+    with pytest.raises(bp.BplgError) as e:
+        bp.tridiag_batched(v, v, v, v, v, 64, 1, plan=bad)
+    assert e.value.code == bp.ERR_INVALID_PLAN
