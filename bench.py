@@ -8,14 +8,17 @@ float32, data resident on the GPU):
   fft      complex64 Stockham FFT, forward and inverse, N in {16, 64, 256,
            1024, 4096}, batch = 2^24 / N signals each
   tridiag  float32 CR/PCR solve, n in {64, 256, 1024, 2048}, 2^24 unknowns each
-  refined  float64-residual refined solve, n = 1024, 2^14 systems
+  refined  float64-residual refined solve, n = 1024, 2^14 systems, stopping
+           once a correction is below 1e-12 max|x|
   scan     inclusive sum scan, int32 and float32, n in {64, 1024, 8192},
            2^26 elements each
 
 Every buffer pair is larger than the 129 MB L2, and consecutive launches touch
 different buffers, so no L2 flush is needed between them.  `value` is the
-total elements processed per second (Gelem/s) over all ranks.  Plans are the
-library's query_plan choice (tuned cache if present, else the analytical
+total elements processed per second (Gelem/s) over all ranks.  Plans: every
+row is tuned before the timed region by the library's learned-cost-model
+(Bayesian optimisation) tuner (--plans learned, the default), or taken from
+bplg_query_plan (--plans query: cached tuned plan, else the analytical
 guideline).
 
 --impl reference times the CPU oracle (test infrastructure) on a bounded
@@ -47,6 +50,7 @@ FFT_TOTAL = 1 << 24
 TRI_TOTAL = 1 << 24
 SCAN_TOTAL = 1 << 26
 REF_N, REF_BATCH = 1024, 1 << 14
+REF_TOL = 1e-12  # refinement stops once a correction is below 1e-12 max|x|, the stated accuracy target
 
 METRIC = "batched scan/FFT/tridiag Gelem/s, %HBM roofline; tuned vs exhaustive-best"
 WORKLOAD = ("fft c2c fwd+inv N=16..4096 batch=2^24/N; tridiag CR/PCR n=64..2048 2^24 unknowns; "
@@ -123,46 +127,90 @@ def dist_setup():
 # ----------------------------------------------------------------- workload
 
 class Workload:
-    """Device buffers for every row of the step, filled from the seeded generators."""
+    """Device buffers for every row of the step, filled from the seeded generators,
+    and the plan each row runs with."""
 
-    def __init__(self, torch, bp, dev, scale: float = 1.0):
+    def __init__(self, torch, bp, dev, scale: float = 1.0, rows=None, plans="learned", plan_json=None,
+                 seed: int = 1):
         self.torch, self.bp, self.dev = torch, bp, dev
-        self.items = []  # (name, op_label, n, batch, elems, bytes, launch_fn, host_in, host_out)
+        self.items = []
+        self.rows = set(rows) if rows else None
+        self.plans_mode = plans
+        self.fixed = plan_json or {}
+        self.seed = seed
+        self.tuning = {"mode": plans, "seconds": 0.0, "evaluations": 0}
         t = torch
         for n in FFT_SIZES:
             batch = max(1, int(FFT_TOTAL * scale) // n)
+            if not self._want("fft_fwd_%d" % n) and not self._want("fft_inv_%d" % n):
+                continue
             z = si.fft_c64(batch, n, stream=100 + n)
             zin = t.from_numpy(z.view(np.float32).reshape(-1)).to(dev)
             zout = t.empty_like(zin)
             for direction, tag in ((-1, "fwd"), (1, "inv")):
-                self._add("fft_%s_%d" % (tag, n), "fft", n, batch, batch * n, 16 * batch * n,
-                          (lambda zi=zin, zo=zout, n=n, b=batch, d=direction:
-                           bp.fft_batched(zi, zo, n, b, d)), [zin], [zout])
+                name = "fft_%s_%d" % (tag, n)
+                if not self._want(name):
+                    continue
+                p = self._plan(name, bp.OP_FFT, bp.F32, n, batch)
+                self._add(name, "fft", n, batch, batch * n, 16 * batch * n,
+                          (lambda zi=zin, zo=zout, n=n, b=batch, d=direction, p=p:
+                           bp.fft_batched(zi, zo, n, b, d, plan=p)), [zin], [zout], p)
         for n in TRI_SIZES:
+            name = "tridiag_%d" % n
+            if not self._want(name):
+                continue
             batch = max(1, int(TRI_TOTAL * scale) // n)
             a, b, c, d, _ = si.tridiag_f32(batch, n, stream=200 + n)
             ts = [t.from_numpy(v).to(dev) for v in (a, b, c, d)]
             x = t.empty_like(ts[0])
-            self._add("tridiag_%d" % n, "tridiag", n, batch, batch * n, 20 * batch * n,
-                      (lambda ts=ts, x=x, n=n, b=batch: bp.tridiag_batched(*ts, x, n, b)), ts, [x])
-        batch = max(1, int(REF_BATCH * scale))
-        a, b, c, d, _ = si.tridiag_f32(batch, REF_N, seed=si.CONFIG_SEEDS["precision"])
-        ts = [t.from_numpy(v).to(dev) for v in (a, b, c, d)]
-        x64 = t.empty((batch, REF_N), dtype=t.float64, device=dev)
-        self._add("refined_%d" % REF_N, "refined", REF_N, batch, batch * REF_N, 24 * batch * REF_N,
-                  (lambda ts=ts, x=x64, b=batch: bp.tridiag_refined(*ts, x, REF_N, b)), ts, [x64])
-        for dname, gen in (("i32", lambda b, n: si.scan_i32(b, n, stream=300 + n)),
-                           ("f32", lambda b, n: si.scan_f32(b, n, stream=400 + n))):
+            p = self._plan(name, bp.OP_TRIDIAG, bp.F32, n, batch)
+            self._add(name, "tridiag", n, batch, batch * n, 20 * batch * n,
+                      (lambda ts=ts, x=x, n=n, b=batch, p=p: bp.tridiag_batched(*ts, x, n, b, plan=p)), ts, [x], p)
+        name = "refined_%d" % REF_N
+        if self._want(name):
+            batch = max(1, int(REF_BATCH * scale))
+            a, b, c, d, _ = si.tridiag_f32(batch, REF_N, seed=si.CONFIG_SEEDS["precision"])
+            ts = [t.from_numpy(v).to(dev) for v in (a, b, c, d)]
+            x64 = t.empty((batch, REF_N), dtype=t.float64, device=dev)
+            self.iters = t.zeros(batch, dtype=t.int32, device=dev)
+            p = self._plan(name, bp.OP_TRIDIAG_REFINED, bp.F32, REF_N, batch)
+            self._add(name, "refined", REF_N, batch, batch * REF_N, 24 * batch * REF_N,
+                      (lambda ts=ts, x=x64, b=batch, p=p, it=self.iters:
+                       bp.tridiag_refined(*ts, x, REF_N, b, tol=REF_TOL, iters=it, plan=p)), ts, [x64], p)
+        for dname, dt, gen in (("i32", bp.I32, lambda b, n: si.scan_i32(b, n, stream=300 + n)),
+                               ("f32", bp.F32, lambda b, n: si.scan_f32(b, n, stream=400 + n))):
             for n in SCAN_SIZES:
+                name = "scan_%s_%d" % (dname, n)
+                if not self._want(name):
+                    continue
                 batch = max(1, int(SCAN_TOTAL * scale) // n)
                 xin = t.from_numpy(gen(batch, n)).to(dev)
                 xout = t.empty_like(xin)
-                self._add("scan_%s_%d" % (dname, n), "scan_" + dname, n, batch, batch * n, 8 * batch * n,
-                          (lambda xi=xin, xo=xout, n=n, b=batch: bp.scan_batched(xi, xo, n, b)), [xin], [xout])
+                p = self._plan(name, bp.OP_SCAN, dt, n, batch)
+                self._add(name, "scan_" + dname, n, batch, batch * n, 8 * batch * n,
+                          (lambda xi=xin, xo=xout, n=n, b=batch, p=p, dt=dt:
+                           bp.scan_batched(xi, xo, n, b, dtype=dt, plan=p)), [xin], [xout], p)
 
-    def _add(self, name, op, n, batch, elems, nbytes, fn, ins, outs):
+    def _want(self, name):
+        return self.rows is None or name in self.rows
+
+    def _plan(self, name, op, dtype, n, batch):
+        bp = self.bp
+        if name in self.fixed:
+            p = bp.make_plan(op, n, self.fixed[name]["P"], self.fixed[name]["spb"],
+                             **{k: v for k, v in self.fixed[name].items() if k not in ("P", "spb", "op", "n", "L", "S")})
+            return p
+        if self.plans_mode == "query":
+            return bp.query_plan(op, dtype, n, batch)
+        t0 = time.time()
+        p, rep = bp.tune_plan(op, dtype, n, batch, bp.TUNE_LEARNED, budget=40, seed=self.seed)
+        self.tuning["seconds"] += time.time() - t0
+        self.tuning["evaluations"] += rep.evaluations
+        return p
+
+    def _add(self, name, op, n, batch, elems, nbytes, fn, ins, outs, plan):
         self.items.append(dict(name=name, op=op, n=n, batch=batch, elems=elems, bytes=nbytes, fn=fn,
-                               ins=ins, outs=outs))
+                               ins=ins, outs=outs, plan=plan))
 
     @property
     def elems(self):
@@ -180,7 +228,9 @@ def run_ours(args):
     torch.cuda.set_device(dev)
     import paper_2310_16214_gb300 as bp
 
-    wl = Workload(torch, bp, dev, scale=args.scale)
+    plan_json = json.loads(args.plan_json) if args.plan_json else None
+    wl = Workload(torch, bp, dev, scale=args.scale, rows=args.rows.split(",") if args.rows else None,
+                  plans=args.plans, plan_json=plan_json, seed=args.seed)
     stream = torch.cuda.current_stream()
     ev = {it["name"]: [] for it in wl.items}
 
@@ -252,8 +302,15 @@ def run_ours(args):
     value = world * wl.elems / (step_ms * 1e-3) / 1e9
     launches_per_step = len(wl.items)
     items_out = {it["name"]: {"ms": round(per_item[it["name"]], 5),
-                              "gb_s": round(it["bytes"] / (per_item[it["name"]] * 1e-3) / 1e9, 1)}
+                              "gb_s": round(it["bytes"] / (per_item[it["name"]] * 1e-3) / 1e9, 1),
+                              "plan": {k: v for k, v in it["plan"].as_dict().items()
+                                       if k in ("P", "L", "spb", "smem_layout", "smem_pad", "io", "cr_switch",
+                                                "shuffle", "pattern")}}
                  for it in wl.items}
+    refined_iters = None
+    if hasattr(wl, "iters"):
+        it_np = wl.iters.cpu().numpy()
+        refined_iters = {"mean": round(float(it_np.mean()), 3), "max": int(it_np.max()), "min": int(it_np.min())}
 
     e2e = measure_e2e(torch, wl, stream, args) if rank == 0 and not args.no_e2e else None
     cpu = cpu_baseline(args) if (rank == 0 and world == 1 and not args.no_cpu) else None
@@ -267,10 +324,10 @@ def run_ours(args):
             "data": "synthetic (seeded SplitMix64, paper-shaped batches)",
             "config": {"workload": WORKLOAD, "elems_per_step_per_gpu": wl.elems,
                        "l2": "inputs larger than L2 (every buffer pair > 129 MB), no flush",
-                       "plans": "query_plan (analytical guideline unless a tuned plan is cached)",
+                       "plans": wl.tuning,
                        "parallelism": "replicas" if world > 1 else "single"},
             "roofline": roofline, "per_op": per_op, "per_launch": items_out,
-            "gpu_launches": launches_per_step * args.steps, "clocks": clocks,
+            "gpu_launches": launches_per_step * args.steps, "clocks": clocks, "refined_corrections": refined_iters,
             "e2e": e2e, "cpu_baseline": cpu,
         }
         print(json.dumps(line))
@@ -457,6 +514,11 @@ def main():
     ap.add_argument("--reps", type=int, default=50)
     ap.add_argument("--bo-budget", type=int, default=40)
     ap.add_argument("--seed", type=int, default=1)
+    ap.add_argument("--rows", default="", help="comma-separated row names to run (default: every row)")
+    ap.add_argument("--plans", default="learned", choices=["learned", "query"],
+                    help="learned: Bayesian-optimisation tuning of every row before the timed region; "
+                         "query: bplg_query_plan (cached tuned plan, else the analytical guideline)")
+    ap.add_argument("--plan-json", default="", help='fixed plans: {"row": {"P": .., "spb": .., knob: ..}}')
     args = ap.parse_args()
     if args.tune_report:
         tune_report(args)

@@ -84,9 +84,16 @@ typedef enum { BPLG_TC_BF16 = 0, BPLG_TC_F16 = 1 } bplg_tc_precision;
  *           BPLG_PATTERN_LF (Fig. 1(f) / 1(d)).
  *   smem_layout FFT: 0 interleaved complex, 1 real and imaginary parts
  *           exchanged in turn through one float buffer (Section V-C).
+ *           Tridiag: 0 all CR levels in place in shared memory, 1 one
+ *           shared-memory array per CR level (stride-free), 2 the first
+ *           log2 P CR levels in registers, the rest in shared memory.
+ *           Refined tridiag: bit 0 coefficients also cached as float64 in
+ *           shared memory, bit 1 one shared-memory array per CR level.
  *   smem_pad 1: pad shared-memory rows against bank conflicts.
  *   io      FFT: 0 registers <-> global memory directly, 1 staged through
- *           shared memory with 16-byte accesses.
+ *           shared memory with 16-byte accesses, 2 persistent blocks fed by
+ *           a ring of bulk asynchronous copies (TMA).  Tridiag: 0 one tile
+ *           per block, 1 persistent blocks fed by bulk asynchronous copies.
  *   cr_switch tridiag: system size m at which cyclic reduction hands over to
  *           parallel cyclic reduction (1 = pure CR, n = pure PCR).
  */
@@ -269,6 +276,13 @@ int bplg_time_plan(const bplg_plan *plan, int32_t dtype, int64_t n, int64_t batc
 /* Validate `plan` for (op, dtype, n) on the current device.
  * Returns BPLG_OK or BPLG_ERR_INVALID_PLAN (reason in bplg_last_error()). */
 int bplg_check_plan(const bplg_plan *plan, int32_t dtype, int64_t n);
+
+/* Device-side status of the current device: *flag receives 0, or the
+ * nonzero code a pipelined kernel recorded when one of its bounded waits on
+ * an asynchronous copy ran out (it then returned early, leaving its outputs
+ * incomplete).  reset != 0 clears the word.  Synchronous.
+ * Errors: INVALID_ARG, CUDA, NO_DEVICE. */
+int bplg_device_status(int32_t *flag, int32_t reset);
 
 /* Message of the last error on the calling thread ("" if none). */
 const char *bplg_last_error(void);

@@ -36,7 +36,8 @@ EXPORTED = [
     "bplg_scan_batched", "bplg_fft_batched", "bplg_tridiag_batched", "bplg_tridiag_refined",
     "bplg_arch_query", "bplg_arch_preset", "bplg_occupancy", "bplg_guideline_select", "bplg_phi",
     "bplg_enumerate_plans", "bplg_plan_resources", "bplg_tune_plan", "bplg_tune_plans_cost",
-    "bplg_query_plan", "bplg_time_plan", "bplg_check_plan", "bplg_last_error", "bplg_version",
+    "bplg_query_plan", "bplg_time_plan", "bplg_check_plan", "bplg_device_status", "bplg_last_error",
+    "bplg_version",
 ]
 
 
@@ -110,6 +111,7 @@ def _load():
         "bplg_query_plan": ([I32_, I32_, I64, I64, PP], ctypes.c_int),
         "bplg_time_plan": ([PP, I32_, I64, I64, I32_, ctypes.POINTER(D)], ctypes.c_int),
         "bplg_check_plan": ([PP, I32_, I64], ctypes.c_int),
+        "bplg_device_status": ([ctypes.POINTER(I32_), I32_], ctypes.c_int),
         "bplg_last_error": ([], ctypes.c_char_p),
         "bplg_version": ([], ctypes.c_int32),
     }
@@ -271,6 +273,13 @@ def time_plan(plan: Plan, dtype: int, n: int, batch: int, reps: int = 25) -> flo
 
 def check_plan(plan: Plan, dtype: int, n: int) -> int:
     return lib.bplg_check_plan(ctypes.byref(plan), dtype, n)
+
+
+def device_status(reset: bool = False) -> int:
+    """Device error word (0 = fine) recorded by the pipelined kernels."""
+    f = ctypes.c_int32()
+    _check(lib.bplg_device_status(ctypes.byref(f), int(reset)))
+    return f.value
 
 
 def version() -> int:

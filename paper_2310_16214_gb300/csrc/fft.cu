@@ -26,6 +26,7 @@
 
 #include "device_util.cuh"
 #include "internal.h"
+#include "tma.cuh"
 
 namespace bplg {
 
@@ -291,6 +292,192 @@ __global__ void __launch_bounds__(MAXT)
     }
 }
 
+// Persistent, TMA-pipelined variant (io = 2).  Grid = the resident-block
+// capacity of the device; each block walks tiles (spb consecutive signals)
+// tile = blockIdx.x, blockIdx.x + gridDim.x, ...  A ring of NS shared-memory
+// slots holds the tiles: one bulk asynchronous copy (cp.async.bulk) per tile,
+// completion tracked by one mbarrier per slot, so while a tile is computed
+// the next NS-1 tiles are already streaming in.  With T >= 32 threads per
+// signal the first stage reads the slot directly (consecutive lanes,
+// conflict-free), the stage exchanges reuse the slot with the padded layout,
+// and the last stage stores straight to global memory (coalesced).  With
+// T < 32 the tile is first re-laid into a padded exchange buffer and written
+// back through it with 16-byte stores.  Waits are bounded: on timeout the
+// block records an error, drains its own copies (bounded) and returns.
+template <int R, int DIR, int PAD, int MAXT, int NS>
+__global__ void __launch_bounds__(MAXT)
+    fft_tma_kernel(const float2 *in, float2 *out, const float2 *__restrict__ tw, int logn, int spb, int64_t batch,
+                   int64_t ntiles, int slot_elems) {
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    __shared__ __align__(8) uint64_t full[NS];
+    constexpr int LR = clog2(R);
+    const int n = 1 << logn;
+    const int logT = logn - LR;
+    const int T = 1 << logT;
+    const int tid = threadIdx.x;
+    const int s = tid >> logT;
+    const int j = tid & (T - 1);
+    const int stride = sig_stride<0, PAD>(n);
+    const bool small = T < 32;
+    float2 *slots = reinterpret_cast<float2 *>(smem_raw);
+    float2 *xbuf = slots + static_cast<size_t>(NS) * slot_elems;
+    const int sbase = s * stride;
+    // issuer state (thread 0 only): loads issued / consumed per slot
+    int issued[NS], consumed[NS];
+#pragma unroll
+    for (int q = 0; q < NS; ++q) issued[q] = consumed[q] = 0;
+
+    auto issue = [&](int64_t tile, int q) {
+        const int64_t sig0 = tile * spb;
+        const int64_t left = batch - sig0;
+        const int nv = left < spb ? static_cast<int>(left) : spb;
+        const uint32_t bytes = static_cast<uint32_t>(nv) * static_cast<uint32_t>(n) * 8u;
+        mbar_arrive_expect_tx(&full[q], bytes);
+        tma_load_1d(slots + static_cast<size_t>(q) * slot_elems, in + sig0 * n, bytes, &full[q]);
+        ++issued[q];
+    };
+
+    if (tid == 0) {
+#pragma unroll
+        for (int q = 0; q < NS; ++q) mbar_init(&full[q], 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    if (tid == 0) {
+#pragma unroll
+        for (int q = 0; q < NS; ++q) {
+            const int64_t tile = blockIdx.x + static_cast<int64_t>(q) * gridDim.x;
+            if (tile < ntiles) issue(tile, q);
+        }
+    }
+
+    int k = 0;
+    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++k) {
+        const int q = k % NS;
+        const uint32_t parity = static_cast<uint32_t>(k / NS) & 1u;
+        float2 *slot = slots + static_cast<size_t>(q) * slot_elems;
+        const int64_t sig0 = tile * spb;
+        const int64_t left = batch - sig0;
+        const int nvalid = left < spb ? static_cast<int>(left) : spb;
+        const bool active = s < nvalid;
+        const bool ok = __syncthreads_and(mbar_wait_bounded(&full[q], parity));
+        if (!ok) {
+            if (tid == 0) {  // drain this block's copies in flight, then leave
+#pragma unroll
+                for (int qq = 0; qq < NS; ++qq)
+                    if (issued[qq] > consumed[qq]) mbar_wait_bounded(&full[qq], static_cast<uint32_t>(consumed[qq]) & 1u);
+            }
+            return;
+        }
+        if (tid == 0) ++consumed[q];
+        const int64_t next = tile + static_cast<int64_t>(NS) * gridDim.x;
+
+        float2 v[R];
+        OutMap om{0, 0, 0, 0, 0, j, T};
+        float2 *ex;
+        if (!small) {
+#pragma unroll
+            for (int m = 0; m < R; ++m) v[m] = slot[s * n + j + m * T];
+            ex = slot;
+        } else {
+            const int count4 = (nvalid * n) >> 1;
+            const float4 *src = reinterpret_cast<const float4 *>(slot);
+            for (int qq = tid; qq < count4; qq += blockDim.x) {
+                const float4 w = src[qq];
+                const int e0 = qq << 1;
+                const int ss = e0 >> logn;
+                const int e = e0 & (n - 1);
+                xbuf[ss * stride + pidx<0, PAD>(e)] = make_float2(w.x, w.y);
+                xbuf[ss * stride + pidx<0, PAD>(e + 1)] = make_float2(w.z, w.w);
+            }
+            __syncthreads();
+            if (tid == 0 && next < ntiles) {
+                fence_proxy_async();
+                issue(next, q);
+            }
+#pragma unroll
+            for (int m = 0; m < R; ++m) v[m] = xbuf[sbase + pidx<0, PAD>(j + m * T)];
+            ex = xbuf;
+        }
+
+        const int lr0 = logn % LR;
+        const int nstages = (lr0 ? 1 : 0) + logn / LR;
+        int logNs = 0;
+        for (int st = 0; st < nstages; ++st) {
+            if (st == 0 && lr0 != 0) {
+                if constexpr (R >= 4) {
+                    if (lr0 == 1) first_stage_mixed<R, 2, DIR>(v);
+                }
+                if constexpr (R >= 8) {
+                    if (lr0 == 2) first_stage_mixed<R, 4, DIR>(v);
+                }
+                if constexpr (R >= 16) {
+                    if (lr0 == 3) first_stage_mixed<R, 8, DIR>(v);
+                }
+                om.mixed = 1;
+                om.lr0 = lr0;
+                om.lq = LR - lr0;
+                logNs = lr0;
+            } else {
+                const int Ns = 1 << logNs;
+                const int kk = j & (Ns - 1);
+                if (logNs > 0) {
+                    const float2 *twp = tw + (Ns << LR);
+#pragma unroll
+                    for (int r = 1; r < R; ++r) {
+                        float2 w = __ldg(twp + r * kk);
+                        if (DIR > 0) w.y = -w.y;
+                        v[r] = cmul(v[r], w);
+                    }
+                }
+                dft_codelet<R, DIR>(v);
+                om.mixed = 0;
+                om.base = ((j >> logNs) << (logNs + LR)) + kk;
+                om.shift = logNs;
+                logNs += LR;
+            }
+            if (st == nstages - 1) break;
+            __syncthreads();
+#pragma unroll
+            for (int r = 0; r < R; ++r) ex[sbase + pidx<0, PAD>(om(r))] = v[r];
+            __syncthreads();
+#pragma unroll
+            for (int m = 0; m < R; ++m) v[m] = ex[sbase + pidx<0, PAD>(j + m * T)];
+        }
+
+        if (!small) {
+            if (active) {
+                float2 *g = out + (sig0 + s) * n;
+#pragma unroll
+                for (int r = 0; r < R; ++r) __stcs(g + om(r), v[r]);
+            }
+            __syncthreads();  // every read of the slot is done: refill it
+            if (tid == 0 && next < ntiles) {
+                fence_proxy_async();
+                issue(next, q);
+            }
+        } else {
+            __syncthreads();
+#pragma unroll
+            for (int r = 0; r < R; ++r) xbuf[sbase + pidx<0, PAD>(om(r))] = v[r];
+            __syncthreads();
+            float4 *g = reinterpret_cast<float4 *>(out + sig0 * n);
+            const int count4 = (nvalid * n) >> 1;
+            for (int qq = tid; qq < count4; qq += blockDim.x) {
+                const int e0 = qq << 1;
+                const int ss = e0 >> logn;
+                const int e = e0 & (n - 1);
+                const float2 lo = xbuf[ss * stride + pidx<0, PAD>(e)];
+                const float2 hi = xbuf[ss * stride + pidx<0, PAD>(e + 1)];
+                __stcs(g + qq, make_float4(lo.x, lo.y, hi.x, hi.y));
+            }
+            __syncthreads();  // xbuf is rewritten by the next tile
+        }
+    }
+}
+
+constexpr int kFftTmaStages = 3;
+
 // Twiddle table: tw[M + k] = exp(-2 pi i k / M) for M = 2, 4, ..., 2^max_log,
 // computed in float64 and rounded once to float32.
 __global__ void twiddle_init_kernel(float2 *tw, int max_log) {
@@ -319,6 +506,7 @@ const void *fft_func_io_t(int io) {
     if constexpr (LAYOUT == 1) {
         return io == 0 ? reinterpret_cast<const void *>(&fft_kernel<R, DIR, 1, PAD, 0, MAXT>) : nullptr;
     } else {
+        if (io == 2) return reinterpret_cast<const void *>(&fft_tma_kernel<R, DIR, PAD, MAXT, kFftTmaStages>);
         return io == 0 ? reinterpret_cast<const void *>(&fft_kernel<R, DIR, 0, PAD, 0, MAXT>)
                        : reinterpret_cast<const void *>(&fft_kernel<R, DIR, 0, PAD, 1, MAXT>);
     }
@@ -350,7 +538,7 @@ const void *fft_func_d(int radix, int layout, int pad, int io, int threads) {
 }
 
 const void *fft_func(int radix, int dir, int layout, int pad, int io, int threads) {
-    if (layout < 0 || layout > 1 || pad < 0 || pad > 1 || io < 0 || io > 1) return nullptr;
+    if (layout < 0 || layout > 1 || pad < 0 || pad > 1 || io < 0 || io > 2) return nullptr;
     return dir < 0 ? fft_func_d<-1>(radix, layout, pad, io, threads)
                    : fft_func_d<1>(radix, layout, pad, io, threads);
 }
@@ -360,8 +548,22 @@ std::unordered_map<int, float2 *> g_tw;
 
 }  // namespace
 
+// elements of one ring slot of the pipelined kernel (128-byte multiple)
+int fft_tma_slot_elems(int pad, int64_t n, int spb) {
+    const int logn = ilog2(n);
+    (void)logn;
+    const int64_t padded = static_cast<int64_t>(spb) * (pad ? sig_stride<0, 1>(static_cast<int>(n)) : static_cast<int>(n));
+    return static_cast<int>((padded + 15) & ~int64_t(15));
+}
+
 int fft_smem_bytes(int radix, int layout, int pad, int io, int64_t n, int spb) {
     const int logn = ilog2(n);
+    if (io == 2) {
+        const int64_t T = n / radix;
+        const int64_t slot = fft_tma_slot_elems(pad, n, spb);
+        const int64_t xb = T < 32 ? static_cast<int64_t>(spb) * (pad ? sig_stride<0, 1>(static_cast<int>(n)) : n) : 0;
+        return static_cast<int>((kFftTmaStages * slot + xb) * 8);
+    }
     const int lr = ilog2(radix);
     const int nstages = (logn % lr ? 1 : 0) + logn / lr;
     if (nstages <= 1 && io == 0) return 0;
@@ -426,10 +628,40 @@ int fft_launch(const bplg_plan &p, const void *in, void *out, int64_t n, int64_t
     if (rc != BPLG_OK) return rc;
     int logn = ilog2(n);
     int spb = p.spb;
+    if (p.io == 2) {
+        int64_t ntiles = li.blocks;
+        int slot_elems = fft_tma_slot_elems(p.smem_pad, n, p.spb);
+        int64_t grid = 0;
+        rc = persistent_grid(li.func, li.threads, li.smem, ntiles, &grid);
+        if (rc != BPLG_OK) return rc;
+        void *args[] = {(void *)&in, (void *)&out, (void *)&tw, &logn, &spb, &batch, &ntiles, &slot_elems};
+        cudaError_t e = cudaLaunchKernel(li.func, dim3(static_cast<unsigned>(grid)), dim3(li.threads), args,
+                                         static_cast<size_t>(li.smem), s);
+        return e == cudaSuccess ? BPLG_OK : launch_error(e, "fft pipelined launch", li.func, grid, li.threads, li.smem);
+    }
     void *args[] = {(void *)&in, (void *)&out, (void *)&tw, &logn, &spb, &batch};
     cudaError_t e = cudaLaunchKernel(li.func, dim3(static_cast<unsigned>(li.blocks)), dim3(li.threads), args,
                                      static_cast<size_t>(li.smem), s);
     return e == cudaSuccess ? BPLG_OK : cuda_error(e, "fft launch");
+}
+
+}  // namespace bplg
+
+namespace bplg {
+
+// Read (and optionally clear) the device error word of this file's kernels
+// on the current device.
+int fft_device_status(int *flag, bool reset) {
+    int v = 0;
+    cudaError_t e = cudaMemcpyFromSymbol(&v, g_device_error, sizeof(int));
+    if (e != cudaSuccess) return cuda_error(e, "device status");
+    if (reset && v) {
+        const int zero = 0;
+        e = cudaMemcpyToSymbol(g_device_error, &zero, sizeof(int));
+        if (e != cudaSuccess) return cuda_error(e, "device status reset");
+    }
+    *flag = v;
+    return BPLG_OK;
 }
 
 }  // namespace bplg

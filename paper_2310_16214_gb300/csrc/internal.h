@@ -14,6 +14,8 @@ namespace bplg {
 // thread-local last-error message; returns `code` for convenient tail calls
 int set_error(int code, const std::string &msg);
 int cuda_error(cudaError_t e, const char *what);
+// cuda_error plus the launch geometry and the kernel's attributes
+int launch_error(cudaError_t e, const char *what, const void *func, int64_t grid, int threads, int smem);
 void clear_error();
 
 inline bool is_pow2(int64_t v) { return v > 0 && (v & (v - 1)) == 0; }
@@ -68,6 +70,8 @@ void plan_finalize(bplg_plan *p, int dtype, int64_t n);
 
 // raise the dynamic shared-memory limit of `func` once per device
 int ensure_smem_attr(const void *func, int smem);
+// grid of a persistent kernel: min(work items, SMs x resident blocks per SM)
+int persistent_grid(const void *func, int threads, int smem, int64_t items, int64_t *grid);
 
 // ---- plan cache (per process) and defaults
 bool cache_lookup(int op, int dtype, int64_t n, int64_t batch, bplg_plan *out);

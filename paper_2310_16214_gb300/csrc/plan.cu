@@ -17,7 +17,7 @@
 namespace bplg {
 
 int fft_smem_bytes(int radix, int layout, int pad, int io, int64_t n, int spb);
-int tridiag_smem_bytes(int pad, int64_t n, int spb, bool refined);
+int tridiag_smem_bytes(int pad, int64_t n, int spb, bool refined, int layout, int io, int log_m, int P);
 
 namespace {
 thread_local std::string t_last_error;
@@ -36,6 +36,21 @@ int cuda_error(cudaError_t e, const char *what) {
 }
 
 void clear_error() { t_last_error.clear(); }
+
+int launch_error(cudaError_t e, const char *what, const void *func, int64_t grid, int threads, int smem) {
+    char buf[512];
+    cudaFuncAttributes fa;
+    std::memset(&fa, 0, sizeof(fa));
+    cudaError_t e2 = cudaFuncGetAttributes(&fa, func);
+    std::snprintf(buf, sizeof(buf),
+                  " [grid %lld, block %d, dynamic smem %d; kernel: regs %d, static smem %zu, local %zu, "
+                  "max threads %d, max dynamic smem %d, attr query %s]",
+                  static_cast<long long>(grid), threads, smem, fa.numRegs, fa.sharedSizeBytes, fa.localSizeBytes,
+                  fa.maxThreadsPerBlock, fa.maxDynamicSharedSizeBytes, cudaGetErrorName(e2));
+    int rc = cuda_error(e, what);
+    t_last_error += buf;
+    return rc;
+}
 
 const char *last_error_cstr() { return t_last_error.c_str(); }
 
@@ -75,9 +90,9 @@ bool plan_structurally_valid(const bplg_plan &p, int dtype, int64_t n, std::stri
             if (p.radix != 2 && p.radix != 4 && p.radix != 8 && p.radix != 16) return fail(why, "radix must be 2, 4, 8 or 16");
             if (p.P != p.radix) return fail(why, "FFT: P must equal the radix");
             if (n < 2) return fail(why, "FFT: n >= 2");
-            if (p.smem_layout < 0 || p.smem_layout > 1 || p.smem_pad < 0 || p.smem_pad > 1 || p.io < 0 || p.io > 1)
+            if (p.smem_layout < 0 || p.smem_layout > 1 || p.smem_pad < 0 || p.smem_pad > 1 || p.io < 0 || p.io > 2)
                 return fail(why, "FFT: layout/pad/io out of range");
-            if (p.smem_layout == 1 && p.io == 1) return fail(why, "FFT: staged io needs the interleaved layout");
+            if (p.smem_layout == 1 && p.io != 0) return fail(why, "FFT: staged and pipelined io need the interleaved layout");
             return true;
         case BPLG_OP_TRIDIAG:
         case BPLG_OP_TRIDIAG_REFINED: {
@@ -89,6 +104,18 @@ bool plan_structurally_valid(const bplg_plan &p, int dtype, int64_t n, std::stri
                 return fail(why, "tridiag: shuffle/pad out of range");
             if (p.shuffle && p.cr_switch > 32) return fail(why, "tridiag: shuffle PCR needs cr_switch <= 32");
             if (p.op == BPLG_OP_TRIDIAG_REFINED && tps < 32) return fail(why, "refined: at least 32 threads per system");
+            if (p.smem_layout < 0 || p.smem_layout > (p.op == BPLG_OP_TRIDIAG_REFINED ? 3 : 2))
+                return fail(why, "tridiag: smem_layout out of range (0 strided rows, 1 compacted levels, 2 register "
+                                 "levels; refined: bit 0 float64 coefficients, bit 1 compacted levels)");
+            if (p.op == BPLG_OP_TRIDIAG && p.smem_layout == 2 && (p.P < 2 || p.io != 0))
+                return fail(why, "tridiag: register levels need P >= 2 and the per-block kernel");
+            if (p.op == BPLG_OP_TRIDIAG && p.smem_layout == 1 && (p.smem_pad != 1 || p.io != 0))
+                return fail(why, "tridiag: the compacted layout is always padded and per-block");
+            if (p.op == BPLG_OP_TRIDIAG_REFINED && (p.smem_layout & 2) && p.smem_pad != 1)
+                return fail(why, "refined: the compacted layout is always padded");
+            if (p.io < 0 || p.io > (p.op == BPLG_OP_TRIDIAG ? 1 : 0))
+                return fail(why, "tridiag: io out of range (0 per-block, 1 pipelined)");
+            if (p.io == 1 && n < 4) return fail(why, "tridiag: the pipelined kernel needs n >= 4");
             return true;
         }
         default:
@@ -101,8 +128,10 @@ int plan_smem_bytes(const bplg_plan &p, int dtype, int64_t n) {
     switch (p.op) {
         case BPLG_OP_SCAN: return 0;
         case BPLG_OP_FFT: return fft_smem_bytes(p.radix, p.smem_layout, p.smem_pad, p.io, n, p.spb);
-        case BPLG_OP_TRIDIAG: return tridiag_smem_bytes(p.smem_pad, n, p.spb, false);
-        case BPLG_OP_TRIDIAG_REFINED: return tridiag_smem_bytes(p.smem_pad, n, p.spb, true);
+        case BPLG_OP_TRIDIAG:
+            return tridiag_smem_bytes(p.smem_pad, n, p.spb, false, p.smem_layout, p.io, ilog2(p.cr_switch), p.P);
+        case BPLG_OP_TRIDIAG_REFINED:
+            return tridiag_smem_bytes(p.smem_pad, n, p.spb, true, p.smem_layout, 0, ilog2(p.cr_switch), p.P);
         default: return 0;
     }
 }
@@ -127,7 +156,8 @@ void plan_finalize(bplg_plan *p, int dtype, int64_t n) {
         case BPLG_OP_TRIDIAG:
         case BPLG_OP_TRIDIAG_REFINED:
             p->radix = 2;
-            p->pattern = p->smem_layout = p->io = 0;
+            p->pattern = 0;
+            if (p->op == BPLG_OP_TRIDIAG_REFINED) p->io = 0;
             p->S = static_cast<int32_t>(p->spb * n);
             break;
         default:
@@ -163,9 +193,9 @@ std::vector<bplg_plan> enumerate_structural(int op, int dtype, int64_t n) {
             } else if (op == BPLG_OP_FFT) {
                 if (P < 2 || P > 16) continue;
                 p.radix = P;
-                const int io_first = tps >= 32 ? 0 : 1;
-                for (int io_i = 0; io_i < 2; ++io_i) {
-                    const int io = io_i == 0 ? io_first : 1 - io_first;
+                const int io_order[3] = {2, tps >= 32 ? 0 : 1, tps >= 32 ? 1 : 0};
+                for (int io_i = 0; io_i < 3; ++io_i) {
+                    const int io = io_order[io_i];
                     for (int layout = 0; layout <= 1; ++layout) {
                         for (int pad = 1; pad >= 0; --pad) {
                             p.io = io;
@@ -177,13 +207,21 @@ std::vector<bplg_plan> enumerate_structural(int op, int dtype, int64_t n) {
                 }
             } else {
                 const int64_t mmax = tps < n ? tps : n;
-                for (int64_t m = mmax; m >= 1; m /= 2) {
-                    for (int sh = 1; sh >= 0; --sh) {
-                        for (int pad = 1; pad >= 0; --pad) {
-                            p.cr_switch = static_cast<int32_t>(m);
-                            p.shuffle = sh;
-                            p.smem_pad = pad;
-                            push(p);
+                const int layouts = op == BPLG_OP_TRIDIAG_REFINED ? 4 : 3;
+                const int ios = op == BPLG_OP_TRIDIAG ? 2 : 1;
+                for (int io = ios - 1; io >= 0; --io) {
+                    for (int lay = layouts - 1; lay >= 0; --lay) {
+                        for (int64_t m = mmax; m >= 1; m /= 2) {
+                            for (int sh = 1; sh >= 0; --sh) {
+                                for (int pad = 1; pad >= 0; --pad) {
+                                    p.cr_switch = static_cast<int32_t>(m);
+                                    p.shuffle = sh;
+                                    p.smem_pad = pad;
+                                    p.smem_layout = lay;
+                                    p.io = io;
+                                    push(p);
+                                }
+                            }
                         }
                     }
                 }
@@ -200,7 +238,7 @@ std::map<std::pair<int, const void *>, int> g_attr;  // (device, func) -> max dy
 }  // namespace
 
 int ensure_smem_attr(const void *func, int smem) {
-    if (smem <= 48 * 1024) return BPLG_OK;
+    if (smem <= 0) return BPLG_OK;
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return cuda_error(e, "cudaGetDevice");
@@ -208,9 +246,42 @@ int ensure_smem_attr(const void *func, int smem) {
     auto key = std::make_pair(dev, func);
     auto it = g_attr.find(key);
     if (it != g_attr.end() && it->second >= smem) return BPLG_OK;
-    e = cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    if (e != cudaSuccess) return cuda_error(e, "cudaFuncSetAttribute(max dynamic smem)");
+    // the default limit (48 KB minus the kernel's static shared memory) is
+    // kept when it suffices; otherwise opt in to the requested size
+    cudaFuncAttributes fa;
+    e = cudaFuncGetAttributes(&fa, func);
+    if (e != cudaSuccess) return cuda_error(e, "cudaFuncGetAttributes");
+    if (fa.maxDynamicSharedSizeBytes < smem) {
+        e = cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        if (e != cudaSuccess) return cuda_error(e, "cudaFuncSetAttribute(max dynamic smem)");
+    }
     g_attr[key] = smem;
+    return BPLG_OK;
+}
+
+int persistent_grid(const void *func, int threads, int smem, int64_t items, int64_t *grid) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_error(e, "cudaGetDevice");
+    static std::mutex mu;
+    static std::map<std::tuple<int, const void *, int, int>, int64_t> cache;
+    std::lock_guard<std::mutex> lock(mu);
+    auto key = std::make_tuple(dev, func, threads, smem);
+    auto it = cache.find(key);
+    int64_t cap;
+    if (it != cache.end()) {
+        cap = it->second;
+    } else {
+        int per_sm = 0, sms = 0;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, func, threads, static_cast<size_t>(smem));
+        if (e != cudaSuccess) return cuda_error(e, "occupancy query");
+        e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (e != cudaSuccess) return cuda_error(e, "cudaDeviceGetAttribute");
+        cap = static_cast<int64_t>(per_sm > 0 ? per_sm : 1) * sms;
+        cache[key] = cap;
+    }
+    *grid = items < cap ? items : cap;
+    if (*grid < 1) *grid = 1;
     return BPLG_OK;
 }
 

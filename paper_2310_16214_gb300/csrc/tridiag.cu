@@ -3,10 +3,11 @@
 // back substitution (Section III, "Tridiagonal system solvers"; knobs of
 // Section V-A).  Equation i is a_i x_{i-1} + b_i x_i + c_i x_{i+1} = d_i.
 //
-// A block holds `spb` systems of n = 2^logn equations in shared memory as four
-// arrays a, b, c, d (structure of arrays, optionally padded by one slot per 32
-// against the bank conflicts of CR's doubling strides); each system is served
-// by tps = n/P threads.
+// A block holds `spb` systems of n = 2^logn equations in shared memory, one
+// float4 (a, b, c, d) per equation, so every CR/PCR step reads or writes an
+// equation with a single 16-byte access.  With smem_pad the row index i is
+// stored at i + i/8 + i/64, which spreads the doubling strides of CR over the
+// shared-memory banks.  Each system is served by tps = n/P threads.
 //
 // CR forward level with stride delta updates the equations i = 2 delta (u+1) - 1
 // from their neighbours i -/+ delta:
@@ -19,93 +20,89 @@
 // shuffles when `shuffle` is set, else through shared memory) until every
 // equation is decoupled, x = d / b.  Back substitution walks the CR levels in
 // reverse: x_i = (d_i - a_i x_{i-delta} - c_i x_{i+delta}) / b_i.  x overwrites
-// d in place.  a_0 and c_{n-1} are never read (treated as 0).
+// d in place.  a_0 and c_{n-1} are never read (treated as 0).  Divisions use
+// the hardware reciprocal (about 1 ulp), well inside the float32 tolerance.
 //
-// The refined variant keeps the original float32 coefficients beside a
-// working copy and x in float64; each correction computes r = d - A x in
-// float64, scales r by a power of two sigma so that max|r sigma| is in
-// [1/2, 1), solves A e' = r sigma in float32 with the same CR/PCR code, and
-// adds e = e' / sigma to x in float64.
+// The refined variant keeps the original coefficients beside a working copy
+// and x in float64; each correction computes r = d - A x in float64 from the
+// stored float32 coefficients, scales r by a power of two sigma so that
+// max|r sigma| is in [1/2, 1), solves A e' = r sigma in float32 with the same
+// CR/PCR code, and adds e = e' / sigma to x in float64.  With smem_layout 1 the
+// coefficients are also cached as float64 in shared memory, so the residual
+// needs no conversions (the float64 pipe is the bottleneck of this kernel).
 #include "device_util.cuh"
 #include "internal.h"
+#include "tma.cuh"
 
 namespace bplg {
 
 template <int PAD>
 __device__ __forceinline__ int tpid(int i) {
-    return PAD ? i + (i >> 5) : i;
+    return PAD ? i + (i >> 3) + (i >> 6) : i;
 }
 
 template <int PAD>
 __host__ __device__ __forceinline__ int tstride(int n) {
-    if (!PAD) return n;
-    int p = n >> 5;
-    return n + (p > 0 ? p : 1);
+    return PAD ? n + (n >> 3) + (n >> 6) + 1 : n;
 }
 
-struct SysArrays {
-    float *a, *b, *c, *d;
-};
+__device__ __forceinline__ float frcp(float x) { return __fdividef(1.0f, x); }
 
-// Cooperative load of the block's tile of one float array into padded rows.
+// The block's tile of the four structure-of-arrays inputs, written as float4
+// rows (a, b, c, d).  Row of system ss starts at rows + ss * row_stride.
 template <int PAD>
-__device__ __forceinline__ void tile_load(const float *g, float *sm, int arr, int arrs, int stride,
-                                          int logn, int count) {
+__device__ __forceinline__ void tile_load_aos(const float *a, const float *b, const float *c, const float *d,
+                                              float4 *rows, int row_stride, int logn, int count) {
     const int n = 1 << logn;
-    const int count4 = logn >= 2 ? (count >> 2) : 0;  // a float4 stays inside one row
-    const float4 *g4 = reinterpret_cast<const float4 *>(g);
-    for (int q = threadIdx.x; q < count4; q += blockDim.x) {
-        float4 w = __ldcs(g4 + q);
-        const int e = q << 2;
-        const int ss = e >> logn;
-        const int i = e & (n - 1);
-        float *row = sm + (ss * arrs + arr) * stride;
-        row[tpid<PAD>(i)] = w.x;
-        row[tpid<PAD>(i + 1)] = w.y;
-        row[tpid<PAD>(i + 2)] = w.z;
-        row[tpid<PAD>(i + 3)] = w.w;
-    }
-    for (int e = (count4 << 2) + threadIdx.x; e < count; e += blockDim.x) {
-        const int ss = e >> logn;
-        const int i = e & (n - 1);
-        sm[(ss * arrs + arr) * stride + tpid<PAD>(i)] = __ldcs(g + e);
+    if (logn >= 2) {  // a float4 of one array stays inside one system
+        const int count4 = count >> 2;
+        for (int q = threadIdx.x; q < count4; q += blockDim.x) {
+            const float4 va = __ldcs(reinterpret_cast<const float4 *>(a) + q);
+            const float4 vb = __ldcs(reinterpret_cast<const float4 *>(b) + q);
+            const float4 vc = __ldcs(reinterpret_cast<const float4 *>(c) + q);
+            const float4 vd = __ldcs(reinterpret_cast<const float4 *>(d) + q);
+            const int e = q << 2;
+            float4 *row = rows + (e >> logn) * row_stride;
+            const int i = e & (n - 1);
+            row[tpid<PAD>(i)] = make_float4(va.x, vb.x, vc.x, vd.x);
+            row[tpid<PAD>(i + 1)] = make_float4(va.y, vb.y, vc.y, vd.y);
+            row[tpid<PAD>(i + 2)] = make_float4(va.z, vb.z, vc.z, vd.z);
+            row[tpid<PAD>(i + 3)] = make_float4(va.w, vb.w, vc.w, vd.w);
+        }
+    } else {
+        for (int e = threadIdx.x; e < count; e += blockDim.x)
+            rows[(e >> logn) * row_stride + tpid<PAD>(e & (n - 1))] =
+                make_float4(__ldcs(a + e), __ldcs(b + e), __ldcs(c + e), __ldcs(d + e));
     }
 }
 
-// CR / PCR / back substitution on the system described by `s`.  Every thread
-// of the block calls this (it synchronises the block); thread t in [0, tps)
-// of each system does that system's share of the work.
+__device__ __forceinline__ float &dcomp(float4 *row, int pi) { return reinterpret_cast<float *>(row + pi)[3]; }
+
+// CR / PCR / back substitution on one system's rows.  Every thread of the
+// block calls this (it synchronises the block); thread t in [0, tps) of each
+// system does that system's share of the work.
 template <int PAD, int SHUFFLE>
-__device__ void cr_pcr_solve(const SysArrays &s, int logn, int log_m, int t, int tps) {
+__device__ void cr_pcr_solve(float4 *row, int logn, int log_m, int t, int tps) {
     const int n = 1 << logn;
     const int levels = logn - log_m;
-#define A_(i) s.a[tpid<PAD>(i)]
-#define B_(i) s.b[tpid<PAD>(i)]
-#define C_(i) s.c[tpid<PAD>(i)]
-#define D_(i) s.d[tpid<PAD>(i)]
     // ---- cyclic reduction, forward
     for (int ld = 0; ld < levels; ++ld) {
         const int delta = 1 << ld;
         const int cnt = n >> (ld + 1);
         for (int u = t; u < cnt; u += tps) {
             const int i = ((u + 1) << (ld + 1)) - 1;
-            const int il = i - delta;
-            const int ir = i + delta;
-            const float k1 = A_(i) / B_(il);
-            float an = -A_(il) * k1;
-            float bn = B_(i) - C_(il) * k1;
-            float dn = D_(i) - D_(il) * k1;
-            float cn = 0.f;
-            if (ir < n) {
-                const float k2 = C_(i) / B_(ir);
-                bn -= A_(ir) * k2;
-                dn -= D_(ir) * k2;
-                cn = -C_(ir) * k2;
+            const float4 E = row[tpid<PAD>(i)];
+            const float4 Lq = row[tpid<PAD>(i - delta)];
+            const float k1 = E.x * frcp(Lq.y);
+            float4 nw = make_float4(-Lq.x * k1, E.y - Lq.z * k1, 0.f, E.w - Lq.w * k1);
+            if (i + delta < n) {
+                const float4 Rq = row[tpid<PAD>(i + delta)];
+                const float k2 = E.z * frcp(Rq.y);
+                nw.y -= Rq.x * k2;
+                nw.w -= Rq.w * k2;
+                nw.z = -Rq.z * k2;
             }
-            A_(i) = an;
-            B_(i) = bn;
-            C_(i) = cn;
-            D_(i) = dn;
+            row[tpid<PAD>(i)] = nw;
         }
         __syncthreads();
     }
@@ -117,73 +114,62 @@ __device__ void cr_pcr_solve(const SysArrays &s, int logn, int log_m, int t, int
             const int width = tps < 32 ? tps : 32;
             const int jj = t;
             const bool live = jj < m;
-            const int i = ((jj + 1) << ls) - 1;
-            float a = 0.f, b = 1.f, c = 0.f, d = 0.f;
-            if (live) {
-                a = A_(i);
-                b = B_(i);
-                c = C_(i);
-                d = D_(i);
-            }
+            const int pi = tpid<PAD>(((jj + 1) << ls) - 1);
+            float4 q = live ? row[pi] : make_float4(0.f, 1.f, 0.f, 0.f);
             for (int sg = 1; sg < m; sg <<= 1) {
-                const float am = __shfl_up_sync(kFullMask, a, sg, width);
-                const float bm = __shfl_up_sync(kFullMask, b, sg, width);
-                const float cm = __shfl_up_sync(kFullMask, c, sg, width);
-                const float dm = __shfl_up_sync(kFullMask, d, sg, width);
-                const float ap = __shfl_down_sync(kFullMask, a, sg, width);
-                const float bp = __shfl_down_sync(kFullMask, b, sg, width);
-                const float cp = __shfl_down_sync(kFullMask, c, sg, width);
-                const float dp = __shfl_down_sync(kFullMask, d, sg, width);
+                const float am = __shfl_up_sync(kFullMask, q.x, sg, width);
+                const float bm = __shfl_up_sync(kFullMask, q.y, sg, width);
+                const float cm = __shfl_up_sync(kFullMask, q.z, sg, width);
+                const float dm = __shfl_up_sync(kFullMask, q.w, sg, width);
+                const float ap = __shfl_down_sync(kFullMask, q.x, sg, width);
+                const float bp = __shfl_down_sync(kFullMask, q.y, sg, width);
+                const float cp = __shfl_down_sync(kFullMask, q.z, sg, width);
+                const float dp = __shfl_down_sync(kFullMask, q.w, sg, width);
                 const bool hm = jj >= sg;
                 const bool hp = jj + sg < m;
-                const float k1 = hm ? a / bm : 0.f;
-                const float k2 = hp ? c / bp : 0.f;
-                const float an = hm ? -am * k1 : 0.f;
-                const float cn = hp ? -cp * k2 : 0.f;
-                const float bn = b - (hm ? cm * k1 : 0.f) - (hp ? ap * k2 : 0.f);
-                const float dn = d - (hm ? dm * k1 : 0.f) - (hp ? dp * k2 : 0.f);
-                a = an;
-                b = bn;
-                c = cn;
-                d = dn;
+                const float k1 = hm ? q.x * frcp(bm) : 0.f;
+                const float k2 = hp ? q.z * frcp(bp) : 0.f;
+                float4 nw;
+                nw.x = hm ? -am * k1 : 0.f;
+                nw.z = hp ? -cp * k2 : 0.f;
+                nw.y = q.y - (hm ? cm * k1 : 0.f) - (hp ? ap * k2 : 0.f);
+                nw.w = q.w - (hm ? dm * k1 : 0.f) - (hp ? dp * k2 : 0.f);
+                q = nw;
             }
-            if (live) D_(i) = d / b;
+            if (live) dcomp(row, pi) = q.w * frcp(q.y);
         }
         __syncthreads();
     } else {
         const int jj = t;
-        const int i = ((jj + 1) << ls) - 1;
+        const int pi = tpid<PAD>(((jj + 1) << ls) - 1);
         for (int sg = 1; sg < m; sg <<= 1) {
-            float an = 0.f, bn = 1.f, cn = 0.f, dn = 0.f;
+            float4 nw = make_float4(0.f, 1.f, 0.f, 0.f);
             if (jj < m) {
-                const float a = A_(i), b = B_(i), c = C_(i), d = D_(i);
-                bn = b;
-                dn = d;
+                const float4 q = row[pi];
+                nw = make_float4(0.f, q.y, 0.f, q.w);
                 if (jj >= sg) {
-                    const int im = i - (sg << ls);
-                    const float k1 = a / B_(im);
-                    an = -A_(im) * k1;
-                    bn -= C_(im) * k1;
-                    dn -= D_(im) * k1;
+                    const float4 qm = row[tpid<PAD>(((jj + 1 - sg) << ls) - 1)];
+                    const float k1 = q.x * frcp(qm.y);
+                    nw.x = -qm.x * k1;
+                    nw.y -= qm.z * k1;
+                    nw.w -= qm.w * k1;
                 }
                 if (jj + sg < m) {
-                    const int ip = i + (sg << ls);
-                    const float k2 = c / B_(ip);
-                    cn = -C_(ip) * k2;
-                    bn -= A_(ip) * k2;
-                    dn -= D_(ip) * k2;
+                    const float4 qp = row[tpid<PAD>(((jj + 1 + sg) << ls) - 1)];
+                    const float k2 = q.z * frcp(qp.y);
+                    nw.z = -qp.z * k2;
+                    nw.y -= qp.x * k2;
+                    nw.w -= qp.w * k2;
                 }
             }
             __syncthreads();
-            if (jj < m) {
-                A_(i) = an;
-                B_(i) = bn;
-                C_(i) = cn;
-                D_(i) = dn;
-            }
+            if (jj < m) row[pi] = nw;
             __syncthreads();
         }
-        if (jj < m) D_(i) = D_(i) / B_(i);
+        if (jj < m) {
+            const float4 q = row[pi];
+            dcomp(row, pi) = q.w * frcp(q.y);
+        }
         __syncthreads();
     }
     // ---- cyclic reduction, back substitution
@@ -192,16 +178,361 @@ __device__ void cr_pcr_solve(const SysArrays &s, int logn, int log_m, int t, int
         const int cnt = n >> (ld + 1);
         for (int u = t; u < cnt; u += tps) {
             const int i = (u << (ld + 1)) + delta - 1;
-            const float xl = (i >= delta) ? D_(i - delta) : 0.f;
-            const float xr = D_(i + delta);
-            D_(i) = (D_(i) - A_(i) * xl - C_(i) * xr) / B_(i);
+            const float4 E = row[tpid<PAD>(i)];
+            const float xl = (i >= delta) ? dcomp(row, tpid<PAD>(i - delta)) : 0.f;
+            const float xr = dcomp(row, tpid<PAD>(i + delta));
+            dcomp(row, tpid<PAD>(i)) = (E.w - E.x * xl - E.z * xr) * frcp(E.y);
         }
         __syncthreads();
     }
-#undef A_
-#undef B_
-#undef C_
-#undef D_
+}
+
+// ---- compacted-level layout (smem_layout 1)
+// Level l of cyclic reduction keeps its n >> l equations in an array of its
+// own: the forward sweep reads equations 2v, 2v+1, 2v+2 of level l and writes
+// the reduced equation v of level l+1, so every shared-memory access has
+// stride 1 or 2 and one pad slot per 8 rows (cpid) makes them conflict-free.
+// Level l, equation v is the original equation (v+1) 2^l - 1.  Every solved
+// x goes to an original-order array (one pad per 32, xpid, conflict-free for
+// the power-of-two strides of back substitution), from which back
+// substitution reads the neighbours and the result is stored with 16-byte
+// writes.
+__device__ __forceinline__ int cpid(int i) { return i + (i >> 3); }
+__device__ __forceinline__ int xpid(int i) { return i + (i >> 5); }
+__host__ __device__ __forceinline__ int compact_level_size(int m) { return m + (m >> 3) + 1; }
+__host__ __device__ __forceinline__ int compact_levels_elems(int n, int levels) {
+    int e = 0;
+    for (int l = 0; l <= levels; ++l) e += compact_level_size(n >> l);
+    return e;
+}
+// bytes of one system: level rows (float4) then x (float), 16-byte multiple
+__host__ __device__ __forceinline__ int compact_sys_bytes(int n, int levels) {
+    const int xb = 4 * (n + (n >> 5) + 1);
+    return 16 * compact_levels_elems(n, levels) + ((xb + 15) & ~15);
+}
+
+template <int SHUFFLE>
+__device__ void cr_pcr_solve_compact(float4 *lv, float *X, int logn, int log_m, int t, int tps) {
+    const int n = 1 << logn;
+    const int levels = logn - log_m;
+    // ---- forward: level l -> level l+1
+    int off = 0;
+    for (int ld = 0; ld < levels; ++ld) {
+        const int ml = n >> ld;
+        const int half = ml >> 1;
+        const int off_next = off + compact_level_size(ml);
+        const float4 *L = lv + off;
+        float4 *N = lv + off_next;
+        for (int v = t; v < half; v += tps) {
+            const int i = 2 * v + 1;
+            const float4 E = L[cpid(i)];
+            const float4 Lq = L[cpid(i - 1)];
+            const float k1 = E.x * frcp(Lq.y);
+            float4 nw = make_float4(-Lq.x * k1, E.y - Lq.z * k1, 0.f, E.w - Lq.w * k1);
+            if (i + 1 < ml) {
+                const float4 Rq = L[cpid(i + 1)];
+                const float k2 = E.z * frcp(Rq.y);
+                nw.y -= Rq.x * k2;
+                nw.w -= Rq.w * k2;
+                nw.z = -Rq.z * k2;
+            }
+            N[cpid(v)] = nw;
+        }
+        off = off_next;
+        __syncthreads();
+    }
+    // ---- PCR on the m contiguous equations of the top level
+    float4 *Tp = lv + off;
+    const int m = 1 << log_m;
+    if constexpr (SHUFFLE) {
+        if (t < 32) {
+            const int width = tps < 32 ? tps : 32;
+            const bool live = t < m;
+            float4 q = live ? Tp[cpid(t)] : make_float4(0.f, 1.f, 0.f, 0.f);
+            for (int sg = 1; sg < m; sg <<= 1) {
+                const float am = __shfl_up_sync(kFullMask, q.x, sg, width);
+                const float bm = __shfl_up_sync(kFullMask, q.y, sg, width);
+                const float cm = __shfl_up_sync(kFullMask, q.z, sg, width);
+                const float dm = __shfl_up_sync(kFullMask, q.w, sg, width);
+                const float ap = __shfl_down_sync(kFullMask, q.x, sg, width);
+                const float bp = __shfl_down_sync(kFullMask, q.y, sg, width);
+                const float cp = __shfl_down_sync(kFullMask, q.z, sg, width);
+                const float dp = __shfl_down_sync(kFullMask, q.w, sg, width);
+                const bool hm = t >= sg;
+                const bool hp = t + sg < m;
+                const float k1 = hm ? q.x * frcp(bm) : 0.f;
+                const float k2 = hp ? q.z * frcp(bp) : 0.f;
+                float4 nw;
+                nw.x = hm ? -am * k1 : 0.f;
+                nw.z = hp ? -cp * k2 : 0.f;
+                nw.y = q.y - (hm ? cm * k1 : 0.f) - (hp ? ap * k2 : 0.f);
+                nw.w = q.w - (hm ? dm * k1 : 0.f) - (hp ? dp * k2 : 0.f);
+                q = nw;
+            }
+            if (live) X[xpid(((t + 1) << levels) - 1)] = q.w * frcp(q.y);
+        }
+    } else {
+        for (int sg = 1; sg < m; sg <<= 1) {
+            float4 nw = make_float4(0.f, 1.f, 0.f, 0.f);
+            if (t < m) {
+                const float4 q = Tp[cpid(t)];
+                nw = make_float4(0.f, q.y, 0.f, q.w);
+                if (t >= sg) {
+                    const float4 qm = Tp[cpid(t - sg)];
+                    const float k1 = q.x * frcp(qm.y);
+                    nw.x = -qm.x * k1;
+                    nw.y -= qm.z * k1;
+                    nw.w -= qm.w * k1;
+                }
+                if (t + sg < m) {
+                    const float4 qp = Tp[cpid(t + sg)];
+                    const float k2 = q.z * frcp(qp.y);
+                    nw.z = -qp.z * k2;
+                    nw.y -= qp.x * k2;
+                    nw.w -= qp.w * k2;
+                }
+            }
+            __syncthreads();
+            if (t < m) Tp[cpid(t)] = nw;
+            __syncthreads();
+        }
+        if (t < m) {
+            const float4 q = Tp[cpid(t)];
+            X[xpid(((t + 1) << levels) - 1)] = q.w * frcp(q.y);
+        }
+    }
+    __syncthreads();
+    // ---- back substitution: the even equations of level l.  Their
+    // neighbours (the odd equations, original indices 2w 2^l - 1 and
+    // (2w+2) 2^l - 1) were solved at higher levels; X holds every solved x.
+    for (int ld = levels - 1; ld >= 0; --ld) {
+        int o = 0;
+        for (int l = 0; l < ld; ++l) o += compact_level_size(n >> l);
+        const float4 *L = lv + o;
+        const int half = (n >> ld) >> 1;
+        for (int w = t; w < half; w += tps) {
+            const float4 E = L[cpid(2 * w)];
+            const float xl = w > 0 ? X[xpid(((2 * w) << ld) - 1)] : 0.f;
+            const float xr = X[xpid(((2 * w + 2) << ld) - 1)];
+            X[xpid(((2 * w + 1) << ld) - 1)] = (E.w - E.x * xl - E.z * xr) * frcp(E.y);
+        }
+        __syncthreads();
+    }
+}
+
+// The block's tile of the four inputs written as level-0 rows of each
+// system's compacted block (system ss at byte ss * sys_bytes).
+__device__ __forceinline__ void tile_load_compact(const float *a, const float *b, const float *c, const float *d,
+                                                  unsigned char *sm, int sys_bytes, int logn, int count) {
+    const int n = 1 << logn;
+    if (logn >= 2) {
+        const int count4 = count >> 2;
+        for (int q = threadIdx.x; q < count4; q += blockDim.x) {
+            const float4 va = __ldcs(reinterpret_cast<const float4 *>(a) + q);
+            const float4 vb = __ldcs(reinterpret_cast<const float4 *>(b) + q);
+            const float4 vc = __ldcs(reinterpret_cast<const float4 *>(c) + q);
+            const float4 vd = __ldcs(reinterpret_cast<const float4 *>(d) + q);
+            const int e = q << 2;
+            float4 *row = reinterpret_cast<float4 *>(sm + (e >> logn) * sys_bytes);
+            const int i = e & (n - 1);
+            row[cpid(i)] = make_float4(va.x, vb.x, vc.x, vd.x);
+            row[cpid(i + 1)] = make_float4(va.y, vb.y, vc.y, vd.y);
+            row[cpid(i + 2)] = make_float4(va.z, vb.z, vc.z, vd.z);
+            row[cpid(i + 3)] = make_float4(va.w, vb.w, vc.w, vd.w);
+        }
+    } else {
+        for (int e = threadIdx.x; e < count; e += blockDim.x)
+            reinterpret_cast<float4 *>(sm + (e >> logn) * sys_bytes)[cpid(e & (n - 1))] =
+                make_float4(__ldcs(a + e), __ldcs(b + e), __ldcs(c + e), __ldcs(d + e));
+    }
+}
+
+__device__ __forceinline__ void tile_store_compact(float *x, unsigned char *sm, int sys_bytes, int x_off, int logn,
+                                                   int count) {
+    const int n = 1 << logn;
+    if (logn >= 2) {
+        const int count4 = count >> 2;
+        for (int q = threadIdx.x; q < count4; q += blockDim.x) {
+            const int e = q << 2;
+            const float *X = reinterpret_cast<const float *>(sm + (e >> logn) * sys_bytes + x_off);
+            const int i = e & (n - 1);
+            __stcs(reinterpret_cast<float4 *>(x) + q,
+                   make_float4(X[xpid(i)], X[xpid(i + 1)], X[xpid(i + 2)], X[xpid(i + 3)]));
+        }
+    } else {
+        for (int e = threadIdx.x; e < count; e += blockDim.x)
+            x[e] = reinterpret_cast<const float *>(sm + (e >> logn) * sys_bytes + x_off)[xpid(e & (n - 1))];
+    }
+}
+
+template <int SHUFFLE>
+__global__ void __launch_bounds__(1024)
+    tridiag_compact_kernel(const float *a, const float *b, const float *c, const float *d, float *x, int logn,
+                           int log_m, int log_tps, int spb, int64_t batch) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int n = 1 << logn;
+    const int tps = 1 << log_tps;
+    const int tid = threadIdx.x;
+    const int s = tid >> log_tps;
+    const int t = tid & (tps - 1);
+    const int levels = logn - log_m;
+    const int sys_bytes = compact_sys_bytes(n, levels);
+    const int x_off = 16 * compact_levels_elems(n, levels);
+    const int64_t sig0 = static_cast<int64_t>(blockIdx.x) * spb;
+    const int64_t left = batch - sig0;
+    const int nvalid = left < spb ? static_cast<int>(left) : spb;
+    const int64_t off = sig0 * n;
+    const int count = nvalid * n;
+    unsigned char *mine = smem_raw + static_cast<size_t>(s) * sys_bytes;
+    float4 *lv = reinterpret_cast<float4 *>(mine);
+    float *X = reinterpret_cast<float *>(mine + x_off);
+
+    tile_load_compact(a + off, b + off, c + off, d + off, smem_raw, sys_bytes, logn, count);
+    __syncthreads();
+    if (s >= nvalid) {
+        for (int i = t; i < n; i += tps) lv[cpid(i)] = make_float4(0.f, 1.f, 0.f, 0.f);
+    }
+    if (t == 0) {
+        lv[cpid(0)].x = 0.f;
+        lv[cpid(n - 1)].z = 0.f;
+    }
+    __syncthreads();
+    cr_pcr_solve_compact<SHUFFLE>(lv, X, logn, log_m, t, tps);
+    tile_store_compact(x + off, smem_raw, sys_bytes, x_off, logn, count);
+}
+
+// ---- register cyclic reduction (smem_layout 2)
+// Each thread owns P consecutive equations in registers and performs the
+// first log2 P levels of cyclic reduction on them there.  At level l the
+// updated equations are the local indices 2^(l+1) k - 1; all of them have
+// their left neighbour in the thread, and all but the last (local P-1) their
+// right one too.  The right neighbour of local P-1 is the next thread's local
+// equation 2^l - 1 as it stands after level l-1, which that thread computes
+// from its own data alone; so every thread first reduces everything except
+// local P-1, publishes those log2 P "boundary" equations through shared
+// memory (one barrier), and then reduces local P-1 with its neighbour's.
+// Local P-1 is then the thread's equation of level log2 P: the n/P of them
+// form a tridiagonal system on consecutive threads that the shared-memory
+// CR/PCR code solves.  Back substitution of the register levels runs in
+// registers again; only the previous thread's last x crosses threads.
+__device__ __forceinline__ void cr_reduce(float &a, float &b, float &c, float &d, float la, float lb, float lc,
+                                          float ld, float ra, float rb, float rc, float rd, bool has_right) {
+    const float k1 = a * frcp(lb);
+    float na = -la * k1, nb = b - lc * k1, nc = 0.f, nd = d - ld * k1;
+    if (has_right) {
+        const float k2 = c * frcp(rb);
+        nb -= ra * k2;
+        nd -= rd * k2;
+        nc = -rc * k2;
+    }
+    a = na;
+    b = nb;
+    c = nc;
+    d = nd;
+}
+
+template <int P, int PAD, int SHUFFLE, int MAXT>
+__global__ void __launch_bounds__(MAXT)
+    tridiag_reg_kernel(const float *ga, const float *gb, const float *gc, const float *gd, float *x, int logn,
+                       int log_m, int log_tps, int spb, int64_t batch) {
+    constexpr int LP = (P >= 16) ? 4 : (P >= 8) ? 3 : (P >= 4) ? 2 : 1;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int n = 1 << logn;
+    const int tps = 1 << log_tps;
+    const int tid = threadIdx.x;
+    const int s = tid >> log_tps;
+    const int t = tid & (tps - 1);
+    const int64_t sig0 = static_cast<int64_t>(blockIdx.x) * spb;
+    const int64_t left = batch - sig0;
+    const int nvalid = left < spb ? static_cast<int>(left) : spb;
+    const bool active = s < nvalid;
+    const int mstride = tstride<PAD>(tps);
+    float4 *rows = reinterpret_cast<float4 *>(smem_raw) + s * mstride;  // middle system of this block's system s
+    float4 *bnd = reinterpret_cast<float4 *>(smem_raw) + spb * mstride;  // [thread][LP] boundary equations
+    const int64_t g = (sig0 + s) * n + static_cast<int64_t>(t) * P;
+
+    float a[P], b[P], c[P], d[P];
+    if (active) {
+        load_run<float, P>(ga + g, a);
+        load_run<float, P>(gb + g, b);
+        load_run<float, P>(gc + g, c);
+        load_run<float, P>(gd + g, d);
+    } else {
+#pragma unroll
+        for (int i = 0; i < P; ++i) {
+            a[i] = 0.f;
+            b[i] = 1.f;
+            c[i] = 0.f;
+            d[i] = 0.f;
+        }
+    }
+    if (t == 0) a[0] = 0.f;
+    if (t == tps - 1) c[P - 1] = 0.f;
+
+    // phase A: every register level except local P-1; record the boundary
+    // equations B_l = local 2^l - 1 as it stands after level l-1
+    bnd[tid * LP + 0] = make_float4(a[0], b[0], c[0], d[0]);
+#pragma unroll
+    for (int l = 0; l < LP; ++l) {
+        const int dl = 1 << l;
+#pragma unroll
+        for (int i = 2 * dl - 1; i < P - 1; i += 2 * dl)
+            cr_reduce(a[i], b[i], c[i], d[i], a[i - dl], b[i - dl], c[i - dl], d[i - dl], a[i + dl], b[i + dl],
+                      c[i + dl], d[i + dl], true);
+        if (l + 1 < LP) {
+            const int q = 2 * dl - 1;
+            bnd[tid * LP + l + 1] = make_float4(a[q], b[q], c[q], d[q]);
+        }
+    }
+    __syncthreads();
+    // phase C: local P-1 through every register level with the next
+    // thread's boundary equations
+    const bool has_next = t < tps - 1;
+#pragma unroll
+    for (int l = 0; l < LP; ++l) {
+        const int dl = 1 << l;
+        float4 r = make_float4(0.f, 1.f, 0.f, 0.f);
+        if (has_next) r = bnd[(tid + 1) * LP + l];
+        cr_reduce(a[P - 1], b[P - 1], c[P - 1], d[P - 1], a[P - 1 - dl], b[P - 1 - dl], c[P - 1 - dl],
+                  d[P - 1 - dl], r.x, r.y, r.z, r.w, has_next);
+    }
+    // the middle system: one equation per thread, consecutive
+    rows[tpid<PAD>(t)] = make_float4(a[P - 1], b[P - 1], c[P - 1], d[P - 1]);
+    __syncthreads();
+    cr_pcr_solve<PAD, SHUFFLE>(rows, log_tps, log_m, t, tps);
+    d[P - 1] = dcomp(rows, tpid<PAD>(t));  // x of local P-1 (d holds x from here on)
+    const float xprev = t > 0 ? dcomp(rows, tpid<PAD>(t - 1)) : 0.f;
+    // back substitution of the register levels
+#pragma unroll
+    for (int l = LP - 1; l >= 0; --l) {
+        const int dl = 1 << l;
+#pragma unroll
+        for (int i = dl - 1; i < P - 1; i += 2 * dl) {
+            const float xl = (i - dl >= 0) ? d[i - dl >= 0 ? i - dl : 0] : xprev;
+            d[i] = (d[i] - a[i] * xl - c[i] * d[i + dl]) * frcp(b[i]);
+        }
+    }
+    if (active) store_run<float, P>(x + g, d);
+}
+
+// Write the x column (the d components) of the block's rows to global memory.
+template <int PAD>
+__device__ __forceinline__ void tile_store_x(float *x, float4 *rows, int row_stride, int logn, int count) {
+    const int n = 1 << logn;
+    if (logn >= 2) {
+        const int count4 = count >> 2;
+        for (int q = threadIdx.x; q < count4; q += blockDim.x) {
+            const int e = q << 2;
+            float4 *row = rows + (e >> logn) * row_stride;
+            const int i = e & (n - 1);
+            __stcs(reinterpret_cast<float4 *>(x) + q,
+                   make_float4(dcomp(row, tpid<PAD>(i)), dcomp(row, tpid<PAD>(i + 1)), dcomp(row, tpid<PAD>(i + 2)),
+                               dcomp(row, tpid<PAD>(i + 3))));
+        }
+    } else {
+        for (int e = threadIdx.x; e < count; e += blockDim.x)
+            x[e] = dcomp(rows + (e >> logn) * row_stride, tpid<PAD>(e & (n - 1)));
+    }
 }
 
 template <int PAD, int SHUFFLE>
@@ -209,7 +540,7 @@ __global__ void __launch_bounds__(1024)
     tridiag_kernel(const float *a, const float *b, const float *c, const float *d, float *x, int logn,
                    int log_m, int log_tps, int spb, int64_t batch) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    float *sm = reinterpret_cast<float *>(smem_raw);
+    float4 *rows = reinterpret_cast<float4 *>(smem_raw);
     const int n = 1 << logn;
     const int tps = 1 << log_tps;
     const int tid = threadIdx.x;
@@ -221,48 +552,121 @@ __global__ void __launch_bounds__(1024)
     const int stride = tstride<PAD>(n);
     const int64_t off = sig0 * n;
     const int count = nvalid * n;
+    float4 *row = rows + s * stride;
 
-    tile_load<PAD>(a + off, sm, 0, 4, stride, logn, count);
-    tile_load<PAD>(b + off, sm, 1, 4, stride, logn, count);
-    tile_load<PAD>(c + off, sm, 2, 4, stride, logn, count);
-    tile_load<PAD>(d + off, sm, 3, 4, stride, logn, count);
-    SysArrays sa;
-    sa.a = sm + (s * 4 + 0) * stride;
-    sa.b = sm + (s * 4 + 1) * stride;
-    sa.c = sm + (s * 4 + 2) * stride;
-    sa.d = sm + (s * 4 + 3) * stride;
+    tile_load_aos<PAD>(a + off, b + off, c + off, d + off, rows, stride, logn, count);
     __syncthreads();
     if (s >= nvalid) {  // systems past the end of the batch: identity rows
-        for (int i = t; i < n; i += tps) {
-            sa.a[tpid<PAD>(i)] = 0.f;
-            sa.b[tpid<PAD>(i)] = 1.f;
-            sa.c[tpid<PAD>(i)] = 0.f;
-            sa.d[tpid<PAD>(i)] = 0.f;
-        }
+        for (int i = t; i < n; i += tps) row[tpid<PAD>(i)] = make_float4(0.f, 1.f, 0.f, 0.f);
     }
     if (t == 0) {
-        sa.a[tpid<PAD>(0)] = 0.f;
-        sa.c[tpid<PAD>(n - 1)] = 0.f;
+        row[tpid<PAD>(0)].x = 0.f;
+        row[tpid<PAD>(n - 1)].z = 0.f;
     }
     __syncthreads();
-    cr_pcr_solve<PAD, SHUFFLE>(sa, logn, log_m, t, tps);
-    // store x (the d rows) with 16-byte accesses
-    float4 *g4 = reinterpret_cast<float4 *>(x + off);
-    const int count4 = logn >= 2 ? (count >> 2) : 0;
-    for (int q = tid; q < count4; q += blockDim.x) {
-        const int e = q << 2;
-        const int ss = e >> logn;
-        const int i = e & (n - 1);
-        const float *row = sm + (ss * 4 + 3) * stride;
-        __stcs(g4 + q, make_float4(row[tpid<PAD>(i)], row[tpid<PAD>(i + 1)], row[tpid<PAD>(i + 2)],
-                                   row[tpid<PAD>(i + 3)]));
+    cr_pcr_solve<PAD, SHUFFLE>(row, logn, log_m, t, tps);
+    tile_store_x<PAD>(x + off, rows, stride, logn, count);
+}
+
+// Persistent, TMA-pipelined variant (io = 1).  Grid = the resident-block
+// capacity; each block walks tiles of spb systems.  A ring of NS slots holds
+// the tiles' four coefficient slices (one bulk asynchronous copy each, one
+// mbarrier per slot), so the next tiles stream in while the current one is
+// reduced.  The slot is unpacked into the padded float4 rows, refilled, and
+// the rows are solved and stored as before.  Waits are bounded: on timeout
+// the block records an error, drains its own copies (bounded) and returns.
+template <int PAD, int SHUFFLE, int NS>
+__global__ void __launch_bounds__(1024)
+    tridiag_tma_kernel(const float *a, const float *b, const float *c, const float *d, float *x, int logn,
+                       int log_m, int log_tps, int spb, int64_t batch, int64_t ntiles) {
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    __shared__ __align__(8) uint64_t full[NS];
+    const int n = 1 << logn;
+    const int tps = 1 << log_tps;
+    const int tid = threadIdx.x;
+    const int s = tid >> log_tps;
+    const int t = tid & (tps - 1);
+    const int stride = tstride<PAD>(n);
+    const int tile_elems = spb * n;  // floats per coefficient slice (multiple of 4)
+    float *slots = reinterpret_cast<float *>(smem_raw);
+    float4 *rows = reinterpret_cast<float4 *>(slots + static_cast<size_t>(NS) * 4 * tile_elems);
+    float4 *row = rows + s * stride;
+    int issued[NS], consumed[NS];
+#pragma unroll
+    for (int q = 0; q < NS; ++q) issued[q] = consumed[q] = 0;
+
+    auto issue = [&](int64_t tile, int q) {
+        const int64_t sig0 = tile * spb;
+        const int64_t left = batch - sig0;
+        const int nv = left < spb ? static_cast<int>(left) : spb;
+        const uint32_t bytes = static_cast<uint32_t>(nv) * static_cast<uint32_t>(n) * 4u;
+        float *dst = slots + static_cast<size_t>(q) * 4 * tile_elems;
+        const int64_t off = sig0 * n;
+        mbar_arrive_expect_tx(&full[q], 4u * bytes);
+        tma_load_1d(dst, a + off, bytes, &full[q]);
+        tma_load_1d(dst + tile_elems, b + off, bytes, &full[q]);
+        tma_load_1d(dst + 2 * tile_elems, c + off, bytes, &full[q]);
+        tma_load_1d(dst + 3 * tile_elems, d + off, bytes, &full[q]);
+        ++issued[q];
+    };
+
+    if (tid == 0) {
+#pragma unroll
+        for (int q = 0; q < NS; ++q) mbar_init(&full[q], 1);
+        fence_mbar_init();
     }
-    for (int e = (count4 << 2) + tid; e < count; e += blockDim.x) {
-        const int ss = e >> logn;
-        const int i = e & (n - 1);
-        x[off + e] = sm[(ss * 4 + 3) * stride + tpid<PAD>(i)];
+    __syncthreads();
+    if (tid == 0) {
+#pragma unroll
+        for (int q = 0; q < NS; ++q) {
+            const int64_t tile = blockIdx.x + static_cast<int64_t>(q) * gridDim.x;
+            if (tile < ntiles) issue(tile, q);
+        }
+    }
+
+    int k = 0;
+    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++k) {
+        const int q = k % NS;
+        const uint32_t parity = static_cast<uint32_t>(k / NS) & 1u;
+        const int64_t sig0 = tile * spb;
+        const int64_t left = batch - sig0;
+        const int nvalid = left < spb ? static_cast<int>(left) : spb;
+        const bool ok = __syncthreads_and(mbar_wait_bounded(&full[q], parity));
+        if (!ok) {
+            if (tid == 0) {
+#pragma unroll
+                for (int qq = 0; qq < NS; ++qq)
+                    if (issued[qq] > consumed[qq]) mbar_wait_bounded(&full[qq], static_cast<uint32_t>(consumed[qq]) & 1u);
+            }
+            return;
+        }
+        if (tid == 0) ++consumed[q];
+        // unpack the slot's slices into float4 rows (identity rows past the batch)
+        const float *sa = slots + static_cast<size_t>(q) * 4 * tile_elems;
+        if (s < nvalid) {
+            const int so = s * n;
+            for (int i = t; i < n; i += tps)
+                row[tpid<PAD>(i)] = make_float4(i > 0 ? sa[so + i] : 0.f, sa[tile_elems + so + i],
+                                                i < n - 1 ? sa[2 * tile_elems + so + i] : 0.f,
+                                                sa[3 * tile_elems + so + i]);
+        } else {
+            for (int i = t; i < n; i += tps) row[tpid<PAD>(i)] = make_float4(0.f, 1.f, 0.f, 0.f);
+        }
+        __syncthreads();
+        if (tid == 0) {
+            const int64_t next = tile + static_cast<int64_t>(NS) * gridDim.x;
+            if (next < ntiles) {
+                fence_proxy_async();
+                issue(next, q);
+            }
+        }
+        cr_pcr_solve<PAD, SHUFFLE>(row, logn, log_m, t, tps);
+        tile_store_x<PAD>(x + sig0 * n, rows, stride, logn, nvalid * n);
+        __syncthreads();  // rows are rebuilt by the next tile
     }
 }
+
+constexpr int kTriTmaStages = 2;
 
 // Maximum of v over the tps >= 32 threads of each system (every thread of the
 // block calls; red holds one slot per warp).
@@ -285,7 +689,17 @@ __device__ __forceinline__ double pow2_f64(int e) {
 }
 __device__ __forceinline__ float pow2_f32(int e) { return __int_as_float((127 + e) << 23); }
 
-template <int PAD, int SHUFFLE>
+// Shared memory of one system in the refined kernel, in bytes (16-byte
+// multiple): the solver's working rows (strided rows, or compacted levels and
+// the original-order x), original float32 rows, optional float64
+// coefficients (a, b) and (c, d) pairs, and x in float64.
+template <int PAD, int COEF64, int SOLVER>
+__host__ __device__ __forceinline__ int refined_sys_bytes(int n, int levels) {
+    const int work = SOLVER ? compact_sys_bytes(n, levels) : 16 * tstride<PAD>(n);
+    return work + 16 * n + (COEF64 ? 32 * n : 0) + 8 * n + (n & 1) * 8;
+}
+
+template <int PAD, int SHUFFLE, int COEF64, int SOLVER>
 __global__ void __launch_bounds__(1024)
     tridiag_refined_kernel(const float *a, const float *b, const float *c, const float *d, double *x,
                            int32_t *iters, int logn, int log_m, int log_tps, int spb, int64_t batch,
@@ -293,7 +707,6 @@ __global__ void __launch_bounds__(1024)
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ float red[32];
     __shared__ int done_sys[32];
-    float *sm = reinterpret_cast<float *>(smem_raw);
     const int n = 1 << logn;
     const int tps = 1 << log_tps;
     const int wps = tps >> 5;
@@ -306,54 +719,59 @@ __global__ void __launch_bounds__(1024)
     const int stride = tstride<PAD>(n);
     const int64_t off = sig0 * n;
     const int count = nvalid * n;
-    // rows: [system][8][stride] floats (original a b c d, working a b c d),
-    // then x as [system][n] doubles
-    const int fl = spb * 8 * stride;
-    double *xs_all = reinterpret_cast<double *>(sm + ((fl + 3) & ~3));
-    double *xs = xs_all + s * n;
-
-    tile_load<PAD>(a + off, sm, 0, 8, stride, logn, count);
-    tile_load<PAD>(b + off, sm, 1, 8, stride, logn, count);
-    tile_load<PAD>(c + off, sm, 2, 8, stride, logn, count);
-    tile_load<PAD>(d + off, sm, 3, 8, stride, logn, count);
-    float *oa = sm + (s * 8 + 0) * stride;
-    float *ob = sm + (s * 8 + 1) * stride;
-    float *oc = sm + (s * 8 + 2) * stride;
-    float *od = sm + (s * 8 + 3) * stride;
-    SysArrays w;
-    w.a = sm + (s * 8 + 4) * stride;
-    w.b = sm + (s * 8 + 5) * stride;
-    w.c = sm + (s * 8 + 6) * stride;
-    w.d = sm + (s * 8 + 7) * stride;
-    __syncthreads();
+    // per system: [work][orig rows][ab64][cd64][x64]
+    const int levels = logn - log_m;
+    const int work_bytes = SOLVER ? compact_sys_bytes(n, levels) : 16 * stride;
+    unsigned char *base = smem_raw + static_cast<size_t>(s) * refined_sys_bytes<PAD, COEF64, SOLVER>(n, levels);
+    float4 *w = reinterpret_cast<float4 *>(base);  // strided rows, or level-0 rows of the compacted layout
+    float *Xc = reinterpret_cast<float *>(base + 16 * compact_levels_elems(n, levels));
+    float4 *o = reinterpret_cast<float4 *>(base + work_bytes);
+    double2 *ab = reinterpret_cast<double2 *>(base + work_bytes + 16 * n);
+    double2 *cd = ab + n;
+    double *xs = reinterpret_cast<double *>(base + work_bytes + 16 * n + (COEF64 ? 32 * n : 0));
+    // working-row index of equation i and the solution of equation i
+    auto widx = [&](int i) { return SOLVER ? cpid(i) : tpid<PAD>(i); };
+    auto xsol = [&](int i) -> float & { return SOLVER ? Xc[xpid(i)] : dcomp(w, tpid<PAD>(i)); };
+    auto solve = [&]() {
+        if constexpr (SOLVER)
+            cr_pcr_solve_compact<SHUFFLE>(w, Xc, logn, log_m, t, tps);
+        else
+            cr_pcr_solve<PAD, SHUFFLE>(w, logn, log_m, t, tps);
+    };
     const bool valid = s < nvalid;
-    for (int i = t; i < n; i += tps) {
-        const int pi = tpid<PAD>(i);
-        if (!valid) {
-            oa[pi] = 0.f;
-            ob[pi] = 1.f;
-            oc[pi] = 0.f;
-            od[pi] = 0.f;
+
+    // load this system's rows (each system reads its own contiguous slices)
+    if (valid) {
+        const int64_t so = off + static_cast<int64_t>(s) * n;
+        for (int i = t; i < n; i += tps) {
+            float4 q = make_float4(i > 0 ? __ldcs(a + so + i) : 0.f, __ldcs(b + so + i),
+                                   i < n - 1 ? __ldcs(c + so + i) : 0.f, __ldcs(d + so + i));
+            o[i] = q;
+            w[widx(i)] = q;
+            if constexpr (COEF64) {
+                ab[i] = make_double2(static_cast<double>(q.x), static_cast<double>(q.y));
+                cd[i] = make_double2(static_cast<double>(q.z), static_cast<double>(q.w));
+            }
         }
-        if (i == 0) oa[pi] = 0.f;
-        if (i == n - 1) oc[pi] = 0.f;
-    }
-    __syncthreads();
-    for (int i = t; i < n; i += tps) {
-        const int pi = tpid<PAD>(i);
-        w.a[pi] = oa[pi];
-        w.b[pi] = ob[pi];
-        w.c[pi] = oc[pi];
-        w.d[pi] = od[pi];
+    } else {
+        for (int i = t; i < n; i += tps) {
+            const float4 q = make_float4(0.f, 1.f, 0.f, 0.f);
+            o[i] = q;
+            w[widx(i)] = q;
+            if constexpr (COEF64) {
+                ab[i] = make_double2(0.0, 1.0);
+                cd[i] = make_double2(0.0, 0.0);
+            }
+        }
     }
     if (t == 0) done_sys[s] = valid ? 0 : 1;
     __syncthreads();
-    cr_pcr_solve<PAD, SHUFFLE>(w, logn, log_m, t, tps);
+    solve();
     // x0 = the float32 solution; max|x0| stands for max|x| in the stopping
     // test (the corrections change x by far less than its magnitude)
     float xmaxf = 0.f;
     for (int i = t; i < n; i += tps) {
-        const float v = w.d[tpid<PAD>(i)];
+        const float v = xsol(i);
         xs[i] = static_cast<double>(v);
         xmaxf = fmaxf(xmaxf, fabsf(v));
     }
@@ -364,19 +782,23 @@ __global__ void __launch_bounds__(1024)
         // residual r = d - A x in float64 from the stored float32 coefficients
         float rmaxf = 0.f;
         for (int i = t; i < n; i += tps) {
-            const int pi = tpid<PAD>(i);
+            const float4 q = o[i];
             const double xl = i > 0 ? xs[i - 1] : 0.0;
             const double xr = i < n - 1 ? xs[i + 1] : 0.0;
-            double r = static_cast<double>(od[pi]);
-            r = fma(-static_cast<double>(oa[pi]), xl, r);
-            r = fma(-static_cast<double>(ob[pi]), xs[i], r);
-            r = fma(-static_cast<double>(oc[pi]), xr, r);
+            double r;
+            if constexpr (COEF64) {
+                const double2 p = ab[i], u = cd[i];
+                r = fma(-p.x, xl, u.y);
+                r = fma(-p.y, xs[i], r);
+                r = fma(-u.x, xr, r);
+            } else {
+                r = fma(-static_cast<double>(q.x), xl, static_cast<double>(q.w));
+                r = fma(-static_cast<double>(q.y), xs[i], r);
+                r = fma(-static_cast<double>(q.z), xr, r);
+            }
             const float rf = static_cast<float>(r);
             rmaxf = fmaxf(rmaxf, fabsf(rf));
-            w.d[pi] = rf;
-            w.a[pi] = oa[pi];
-            w.b[pi] = ob[pi];
-            w.c[pi] = oc[pi];
+            w[widx(i)] = make_float4(q.x, q.y, q.z, rf);
         }
         rmaxf = system_max(rmaxf, red, wps);
         // sigma = 2^-ex brings max|r sigma| into [1/2, 1); the exponent is
@@ -385,14 +807,14 @@ __global__ void __launch_bounds__(1024)
         if (rmaxf > 0.f) frexpf(rmaxf, &ex);
         ex = ex < -120 ? -120 : (ex > 120 ? 120 : ex);
         const float sigma = pow2_f32(-ex);
-        for (int i = t; i < n; i += tps) w.d[tpid<PAD>(i)] *= sigma;
+        for (int i = t; i < n; i += tps) dcomp(w, widx(i)) *= sigma;
         __syncthreads();
-        cr_pcr_solve<PAD, SHUFFLE>(w, logn, log_m, t, tps);
+        solve();
         const bool was_done = done_sys[s] != 0 || rmaxf == 0.f;
         const double inv_sigma = pow2_f64(ex);
         float emaxf = 0.f;
         for (int i = t; i < n; i += tps) {
-            const float ep = w.d[tpid<PAD>(i)];
+            const float ep = xsol(i);
             if (!was_done) xs[i] = fma(static_cast<double>(ep), inv_sigma, xs[i]);
             emaxf = fmaxf(emaxf, fabsf(ep));
         }
@@ -407,51 +829,85 @@ __global__ void __launch_bounds__(1024)
         if (all_done) break;
     }
 
-    // store x (float64, 16-byte accesses) and the correction counts
-    const int count2 = count >> 1;
-    double2 *g2 = reinterpret_cast<double2 *>(x + off);
-    for (int q = tid; q < count2; q += blockDim.x) {
-        const int e = q << 1;
-        __stcs(g2 + q, make_double2(xs_all[e], xs_all[e + 1]));
+    // store x (float64) and the correction counts
+    if (valid) {
+        double *xg = x + off + static_cast<int64_t>(s) * n;
+        for (int i = 2 * t; i < n; i += 2 * tps)
+            __stcs(reinterpret_cast<double2 *>(xg + i), make_double2(xs[i], xs[i + 1]));
+        if (iters && t == 0) iters[sig0 + s] = applied;
     }
-    if ((count & 1) && tid == 0) x[off + count - 1] = xs_all[count - 1];
-    if (iters && t == 0 && valid) iters[sig0 + s] = applied;
 }
 
 namespace {
 
-template <int PAD>
-const void *tri_func_p(int shuffle, bool refined) {
-    if (refined)
-        return shuffle ? reinterpret_cast<const void *>(&tridiag_refined_kernel<PAD, 1>)
-                       : reinterpret_cast<const void *>(&tridiag_refined_kernel<PAD, 0>);
-    return shuffle ? reinterpret_cast<const void *>(&tridiag_kernel<PAD, 1>)
-                   : reinterpret_cast<const void *>(&tridiag_kernel<PAD, 0>);
+// refined: layout bit 0 = float64 coefficient cache, bit 1 = compacted solver
+template <int PAD, int SHUFFLE>
+const void *tri_func_ps(bool refined, int layout, int io, int P) {
+    if (refined) {
+        switch (layout) {
+            case 0: return reinterpret_cast<const void *>(&tridiag_refined_kernel<PAD, SHUFFLE, 0, 0>);
+            case 1: return reinterpret_cast<const void *>(&tridiag_refined_kernel<PAD, SHUFFLE, 1, 0>);
+            case 2: return reinterpret_cast<const void *>(&tridiag_refined_kernel<PAD, SHUFFLE, 0, 1>);
+            default: return reinterpret_cast<const void *>(&tridiag_refined_kernel<PAD, SHUFFLE, 1, 1>);
+        }
+    }
+    if (layout == 1) return reinterpret_cast<const void *>(&tridiag_compact_kernel<SHUFFLE>);
+    if (layout == 2) {
+        switch (P) {
+            case 2: return reinterpret_cast<const void *>(&tridiag_reg_kernel<2, PAD, SHUFFLE, 1024>);
+            case 4: return reinterpret_cast<const void *>(&tridiag_reg_kernel<4, PAD, SHUFFLE, 1024>);
+            case 8: return reinterpret_cast<const void *>(&tridiag_reg_kernel<8, PAD, SHUFFLE, 512>);
+            case 16: return reinterpret_cast<const void *>(&tridiag_reg_kernel<16, PAD, SHUFFLE, 256>);
+            default: return nullptr;
+        }
+    }
+    if (io == 1) return reinterpret_cast<const void *>(&tridiag_tma_kernel<PAD, SHUFFLE, kTriTmaStages>);
+    return reinterpret_cast<const void *>(&tridiag_kernel<PAD, SHUFFLE>);
 }
 
-const void *tri_func(int pad, int shuffle, bool refined) {
-    if (pad < 0 || pad > 1 || shuffle < 0 || shuffle > 1) return nullptr;
-    return pad ? tri_func_p<1>(shuffle, refined) : tri_func_p<0>(shuffle, refined);
+const void *tri_func(int pad, int shuffle, bool refined, int layout, int io, int P) {
+    if (pad < 0 || pad > 1 || shuffle < 0 || shuffle > 1 || layout < 0 || layout > 3 || io < 0 || io > 1)
+        return nullptr;
+    if (!refined && layout == 1 && (pad != 1 || io != 0)) return nullptr;
+    if (!refined && layout == 2 && io != 0) return nullptr;
+    if (pad) return shuffle ? tri_func_ps<1, 1>(refined, layout, io, P) : tri_func_ps<1, 0>(refined, layout, io, P);
+    return shuffle ? tri_func_ps<0, 1>(refined, layout, io, P) : tri_func_ps<0, 0>(refined, layout, io, P);
 }
 
 }  // namespace
 
-int tridiag_smem_bytes(int pad, int64_t n, int spb, bool refined) {
-    const int stride = pad ? tstride<1>(static_cast<int>(n)) : static_cast<int>(n);
-    if (!refined) return spb * 4 * stride * 4;
-    const int fl = (spb * 8 * stride + 3) & ~3;
-    return fl * 4 + spb * static_cast<int>(n) * 8;
+int tridiag_smem_bytes(int pad, int64_t n, int spb, bool refined, int layout, int io, int log_m, int P) {
+    const int ni = static_cast<int>(n);
+    const int levels = ilog2(n) - log_m;
+    if (!refined && layout == 1) return spb * compact_sys_bytes(ni, levels);
+    if (!refined && layout == 2) {
+        // middle rows per system + [threads][log2 P] boundary equations
+        const int tps = ni / P;
+        const int lp = ilog2(P);
+        return spb * 16 * (pad ? tstride<1>(tps) : tps) + spb * tps * lp * 16;
+    }
+    if (!refined && io == 1) return kTriTmaStages * 16 * spb * ni + spb * 16 * (pad ? tstride<1>(ni) : ni);
+    if (!refined) return spb * 16 * (pad ? tstride<1>(ni) : ni);
+    int per = 0;
+    switch (layout) {
+        case 0: per = pad ? refined_sys_bytes<1, 0, 0>(ni, levels) : refined_sys_bytes<0, 0, 0>(ni, levels); break;
+        case 1: per = pad ? refined_sys_bytes<1, 1, 0>(ni, levels) : refined_sys_bytes<0, 1, 0>(ni, levels); break;
+        case 2: per = refined_sys_bytes<1, 0, 1>(ni, levels); break;
+        default: per = refined_sys_bytes<1, 1, 1>(ni, levels); break;
+    }
+    return spb * per;
 }
 
 bool tridiag_launch_info(const bplg_plan &p, int64_t n, int64_t batch, bool refined, Launch *out) {
     std::string why;
     bplg_plan q = p;
     if (!plan_structurally_valid(q, BPLG_F32, n, &why)) return false;
-    const void *f = tri_func(p.smem_pad, p.shuffle, refined);
+    const void *f = tri_func(p.smem_pad, p.shuffle, refined, p.smem_layout, refined ? 0 : p.io, p.P);
     if (!f) return false;
     out->func = f;
     out->threads = p.L;
-    out->smem = tridiag_smem_bytes(p.smem_pad, n, p.spb, refined);
+    out->smem = tridiag_smem_bytes(p.smem_pad, n, p.spb, refined, p.smem_layout, refined ? 0 : p.io, ilog2(p.cr_switch),
+                                   p.P);
     out->blocks = (batch + p.spb - 1) / p.spb;
     return true;
 }
@@ -464,6 +920,17 @@ int tridiag_launch(const bplg_plan &p, const float *a, const float *b, const flo
     int rc = ensure_smem_attr(li.func, li.smem);
     if (rc != BPLG_OK) return rc;
     int logn = ilog2(n), log_m = ilog2(p.cr_switch), log_tps = ilog2(n / p.P), spb = p.spb;
+    if (p.io == 1) {
+        int64_t ntiles = li.blocks, grid = 0;
+        rc = persistent_grid(li.func, li.threads, li.smem, ntiles, &grid);
+        if (rc != BPLG_OK) return rc;
+        void *args[] = {(void *)&a, (void *)&b, (void *)&c, (void *)&d, (void *)&x, &logn, &log_m, &log_tps, &spb, &batch,
+                        &ntiles};
+        cudaError_t e = cudaLaunchKernel(li.func, dim3(static_cast<unsigned>(grid)), dim3(li.threads), args,
+                                         static_cast<size_t>(li.smem), s);
+        return e == cudaSuccess ? BPLG_OK
+                                : launch_error(e, "tridiag pipelined launch", li.func, grid, li.threads, li.smem);
+    }
     void *args[] = {(void *)&a, (void *)&b, (void *)&c, (void *)&d, (void *)&x, &logn, &log_m, &log_tps, &spb, &batch};
     cudaError_t e = cudaLaunchKernel(li.func, dim3(static_cast<unsigned>(li.blocks)), dim3(li.threads), args,
                                      static_cast<size_t>(li.smem), s);
@@ -484,6 +951,25 @@ int tridiag_refined_launch(const bplg_plan &p, const float *a, const float *b, c
     cudaError_t e = cudaLaunchKernel(li.func, dim3(static_cast<unsigned>(li.blocks)), dim3(li.threads), args,
                                      static_cast<size_t>(li.smem), s);
     return e == cudaSuccess ? BPLG_OK : cuda_error(e, "tridiag refined launch");
+}
+
+}  // namespace bplg
+
+namespace bplg {
+
+// Read (and optionally clear) the device error word of this file's kernels
+// on the current device.
+int tridiag_device_status(int *flag, bool reset) {
+    int v = 0;
+    cudaError_t e = cudaMemcpyFromSymbol(&v, g_device_error, sizeof(int));
+    if (e != cudaSuccess) return cuda_error(e, "device status");
+    if (reset && v) {
+        const int zero = 0;
+        e = cudaMemcpyToSymbol(g_device_error, &zero, sizeof(int));
+        if (e != cudaSuccess) return cuda_error(e, "device status reset");
+    }
+    *flag = v;
+    return BPLG_OK;
 }
 
 }  // namespace bplg

@@ -243,11 +243,15 @@ struct SplitMix {
     }
 };
 
-// knob vector of a plan, before normalisation
+// knob vector of a plan, before normalisation: log2 of the graded knobs, the
+// binary knobs as 0/1, and the categorical knobs (shared-memory layout, io
+// mode) one-hot, so that two layouts are equally far apart
 std::vector<double> raw_features(const bplg_plan &p) {
-    return {std::log2(double(p.P)), std::log2(double(p.spb)), double(p.pattern), double(p.smem_layout),
-            double(p.smem_pad),     double(p.io),                std::log2(double(std::max(1, p.cr_switch))),
-            double(p.shuffle)};
+    std::vector<double> f = {std::log2(double(p.P)), std::log2(double(p.spb)), double(p.pattern),
+                             double(p.smem_pad), std::log2(double(std::max(1, p.cr_switch))), double(p.shuffle)};
+    for (int k = 0; k < 4; ++k) f.push_back(p.smem_layout == k ? 1.0 : 0.0);
+    for (int k = 0; k < 3; ++k) f.push_back(p.io == k ? 1.0 : 0.0);
+    return f;
 }
 
 std::vector<std::vector<double>> encode(const std::vector<bplg_plan> &plans) {
@@ -453,7 +457,11 @@ int tune_search(const std::vector<bplg_plan> &plans, const std::vector<int> &reg
     } else if (method == BPLG_TUNE_LEARNED) {
         if (budget <= 0) budget = 40;
         SplitMix rng{seed ^ 0x5DEECE66Dull};
-        const int n0 = std::min(std::min(5, N), budget);
+        // initial random design: 5 points, growing with the square root of
+        // the space (about 2 % of a 1000-plan space), within the budget
+        int n0 = static_cast<int>(std::ceil(0.6 * std::sqrt(static_cast<double>(N))));
+        n0 = std::max(5, std::min(n0, 24));
+        n0 = std::min(std::min(n0, N), budget);
         // seeded initial sample without replacement
         std::vector<int> perm(N);
         std::iota(perm.begin(), perm.end(), 0);

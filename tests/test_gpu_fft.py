@@ -96,3 +96,8 @@ def test_argument_errors(bp):
     with pytest.raises(bp.BplgError) as e:
         bp.fft_batched(z, z, 64, 1, plan=bad)
     assert e.value.code == bp.ERR_INVALID_PLAN
+
+
+def test_no_device_error_recorded(bp):
+    # every pipelined launch above completed its bounded waits
+    assert bp.device_status() == 0

@@ -108,6 +108,16 @@ def test_refined_full_config_sampled(bp):
     assert it.min() >= 1
 
 
+def test_refined_at_the_target_tolerance(bp):
+    # stopping at tol = 1e-12 (the benchmark's setting) still meets 1e-12
+    n, batch = 1024, 256
+    sysm = si.tridiag_f32(batch, n, seed=si.CONFIG_SEEDS["precision"], stream=5)
+    ref = oracle.thomas(*sysm[:4])
+    x, it = run_refined(bp, sysm, tol=1e-12)
+    assert tri_rel_err(x, ref).max() <= 1e-12
+    assert it.min() >= 1
+
+
 def test_refined_zero_iterations_is_the_float32_solve(bp):
     n, batch = 256, 4
     sysm = si.tridiag_f32(batch, n, stream=77)
@@ -133,3 +143,8 @@ def test_argument_errors(bp):
     with pytest.raises(bp.BplgError) as e:
         bp.tridiag_batched(v, v, v, v, v, 64, 1, plan=bad)
     assert e.value.code == bp.ERR_INVALID_PLAN
+
+
+def test_no_device_error_recorded(bp):
+    # every pipelined launch above completed its bounded waits
+    assert bp.device_status() == 0
