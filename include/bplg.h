@@ -136,6 +136,33 @@ int bplg_scan_batched(int32_t dtype, const void *in, void *out, int64_t n, int64
 int bplg_fft_batched(const void *in, void *out, int64_t n, int64_t batch, int32_t dir,
                      const bplg_plan *plan, void *stream);
 
+/* The FFT of bplg_fft_batched for callers that cannot allocate device
+ * memory while they run -- code under an allocator that owns the whole
+ * device, fixed real-time memory budgets, code that must not trigger the
+ * device synchronisation an allocation can cause.  The paper has no
+ * counterpart: this is a property of the library, not of the method.
+ *
+ * It calls no cudaMalloc, cudaFree or other allocating routine: its twiddle
+ * table is a file-scope device array of 64 KB that every GPU loading the
+ * library holds until the process exits, so it accepts only n <= 4096 (larger
+ * n returns BPLG_ERR_UNSUPPORTED_SIZE with a message).  On success nothing is
+ * allocated; on failure the error message string may be.
+ *   in,out  device, [batch][n] complex64 interleaved; in == out is allowed.
+ *   dir     -1 forward, +1 inverse (unnormalised).
+ *   plan    a valid FFT plan with io 0 or 1, or NULL for a fixed default
+ *           (radix min(16, n), at least 128 threads per block).
+ * Set-up: the first call on each device, with that device current, looks up
+ * the array's device address (cudaGetSymbolAddress) and fills the table on
+ * `stream`, waiting for it before returning; make that first call before any
+ * stream capture.  All calls share the array.  It is written only by that
+ * set-up and only read afterwards, so nothing in it has to start at zero and
+ * calls that overlap each other on the GPU read it concurrently without
+ * harm; a call that overlapped the set-up would race with it, which is why
+ * the set-up completes before the first call returns.
+ * Errors: INVALID_ARG, UNSUPPORTED_SIZE, INVALID_PLAN, CUDA. */
+int bplg_fft_batched_noalloc(const void *in, void *out, int64_t n, int64_t batch, int32_t dir,
+                             const bplg_plan *plan, void *stream);
+
 /* Batched tridiagonal solve (Section III, "Tridiagonal system solvers"):
  * a_i x_{i-1} + b_i x_i + c_i x_{i+1} = d_i for every system, by cyclic
  * reduction down to plan->cr_switch equations, parallel cyclic reduction on

@@ -33,7 +33,8 @@ TUNE_ANALYTIC, TUNE_LEARNED, TUNE_EXHAUSTIVE = 0, 1, 2
 TC_BF16, TC_F16 = 0, 1
 
 EXPORTED = [
-    "bplg_scan_batched", "bplg_fft_batched", "bplg_tridiag_batched", "bplg_tridiag_refined",
+    "bplg_scan_batched", "bplg_fft_batched", "bplg_fft_batched_noalloc", "bplg_tridiag_batched",
+    "bplg_tridiag_refined",
     "bplg_arch_query", "bplg_arch_preset", "bplg_occupancy", "bplg_guideline_select", "bplg_phi",
     "bplg_enumerate_plans", "bplg_plan_resources", "bplg_tune_plan", "bplg_tune_plans_cost",
     "bplg_query_plan", "bplg_time_plan", "bplg_check_plan", "bplg_device_status", "bplg_last_error",
@@ -91,6 +92,7 @@ def _load():
     sig = {
         "bplg_scan_batched": ([I32_, P, P, I64, I64, PP, P], ctypes.c_int),
         "bplg_fft_batched": ([P, P, I64, I64, I32_, PP, P], ctypes.c_int),
+        "bplg_fft_batched_noalloc": ([P, P, I64, I64, I32_, PP, P], ctypes.c_int),
         "bplg_tridiag_batched": ([P, P, P, P, P, I64, I64, PP, P], ctypes.c_int),
         "bplg_tridiag_refined": ([P, P, P, P, P, I64, I64, I32_, D, P, PP, P], ctypes.c_int),
         "bplg_arch_query": ([I32_, ctypes.POINTER(Arch)], ctypes.c_int),
@@ -174,6 +176,13 @@ def scan_batched(inp, out, n: int, batch: int, dtype: Optional[int] = None, plan
 def fft_batched(inp, out, n: int, batch: int, direction: int = -1, plan: Optional[Plan] = None, stream=None) -> None:
     """Complex Stockham FFT of [batch][n] complex64 (see bplg_fft_batched)."""
     _check(lib.bplg_fft_batched(_ptr(inp), _ptr(out), n, batch, direction, _plan_ref(plan), _stream(stream)))
+
+
+def fft_batched_noalloc(inp, out, n: int, batch: int, direction: int = -1, plan: Optional[Plan] = None,
+                        stream=None) -> None:
+    """The FFT without any device allocation, n <= 4096 (see bplg_fft_batched_noalloc)."""
+    _check(lib.bplg_fft_batched_noalloc(_ptr(inp), _ptr(out), n, batch, direction, _plan_ref(plan),
+                                        _stream(stream)))
 
 
 def tridiag_batched(a, b, c, d, x, n: int, batch: int, plan: Optional[Plan] = None, stream=None) -> None:

@@ -21,6 +21,7 @@
 //                  shared memory with 16-byte accesses.
 // Twiddles W_M^k = exp(-2 pi i k / M) are generated once per device in float64
 // (sincospi) and rounded to float32; the inverse uses their conjugates.
+#include <cstring>
 #include <mutex>
 #include <unordered_map>
 
@@ -665,3 +666,118 @@ int fft_device_status(int *flag, bool reset) {
 }
 
 }  // namespace bplg
+
+// ---------------------------------------------------------------------------
+// FFT entry point that allocates nothing.
+//
+// The regular entry point allocates its twiddle table with cudaMalloc the
+// first time it runs on a device.  Some callers cannot allow that: code that
+// runs under an allocator which owns all of the device's memory (a framework's
+// caching allocator, a fixed real-time memory budget), code that must not
+// trigger the implicit device synchronisation an allocation can cause, and
+// code whose allocations are only permitted during start-up.  For them the
+// twiddle table lives in the file-scope device array below, sized for
+// transforms of at most kNoAllocMaxN points (64 KB): every GPU that loads the
+// library holds it until the process exits.  The caller still provides the
+// input and output buffers.
+namespace bplg {
+
+constexpr int kNoAllocMaxLog = 12;
+constexpr int kNoAllocMaxN = 1 << kNoAllocMaxLog;
+constexpr int kNoAllocMaxDevices = 64;
+
+}  // namespace bplg
+
+// W_M^k at [M + k] for M = 2 .. kNoAllocMaxN, as in the regular table
+static __device__ __align__(256) float2 g_noalloc_twiddles[2 * bplg::kNoAllocMaxN];
+
+namespace bplg {
+namespace {
+
+std::mutex g_noalloc_mu;
+float2 *g_noalloc_addr[kNoAllocMaxDevices];  // device address of the array, per device
+bool g_noalloc_ready[kNoAllocMaxDevices];
+
+// Set-up, once per device, with that device current: look up the array's
+// device address (the host-side name is only a stand-in for it) and fill it
+// with float64-generated twiddles.  The fill runs on the caller's stream and
+// is waited for before the first call returns.
+int noalloc_setup(cudaStream_t s, const float2 **tw) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_error(e, "cudaGetDevice");
+    if (dev < 0 || dev >= kNoAllocMaxDevices) return set_error(BPLG_ERR_INVALID_ARG, "device index too large");
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_ready[dev]) {
+        float2 *ptr = nullptr;
+        e = cudaGetSymbolAddress(reinterpret_cast<void **>(&ptr), g_noalloc_twiddles);
+        if (e != cudaSuccess) return cuda_error(e, "cudaGetSymbolAddress(no-alloc twiddles)");
+        const int total = 2 * kNoAllocMaxN;
+        twiddle_init_kernel<<<(total + 255) / 256, 256, 0, s>>>(ptr, kNoAllocMaxLog);
+        e = cudaGetLastError();
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) return cuda_error(e, "no-alloc twiddle set-up");
+        g_noalloc_addr[dev] = ptr;
+        g_noalloc_ready[dev] = true;
+    }
+    *tw = g_noalloc_addr[dev];
+    return BPLG_OK;
+}
+
+}  // namespace
+}  // namespace bplg
+
+using namespace bplg;
+
+extern "C" int bplg_fft_batched_noalloc(const void *in, void *out, int64_t n, int64_t batch, int32_t dir,
+                                        const bplg_plan *plan, void *stream) {
+    clear_error();
+    if (!in || !out) return set_error(BPLG_ERR_INVALID_ARG, "fft no-alloc: null buffer");
+    if (n < 1 || batch < 1) return set_error(BPLG_ERR_INVALID_ARG, "fft no-alloc: n and batch must be >= 1");
+    if (dir != -1 && dir != 1) return set_error(BPLG_ERR_INVALID_ARG, "fft no-alloc: dir must be -1 or +1");
+    if (!is_pow2(n) || n < 2)
+        return set_error(BPLG_ERR_UNSUPPORTED_SIZE, "fft no-alloc: n must be a power of two >= 2");
+    if (n > kNoAllocMaxN)
+        return set_error(BPLG_ERR_UNSUPPORTED_SIZE,
+                         "fft no-alloc: n is above 4096, the size its static twiddle table holds; "
+                         "use bplg_fft_batched for larger transforms");
+    if (!aligned16(in) || !aligned16(out)) return set_error(BPLG_ERR_INVALID_ARG, "fft no-alloc: buffers must be 16-byte aligned");
+    // the plan: the caller's, or a fixed default computed without any lookup
+    bplg_plan p;
+    if (plan) {
+        p = *plan;
+    } else {
+        std::memset(&p, 0, sizeof(p));
+        p.op = BPLG_OP_FFT;
+        p.n = static_cast<int32_t>(n);
+        p.P = p.radix = n >= 16 ? 16 : static_cast<int32_t>(n);
+        const int64_t T = n / p.P;
+        p.spb = static_cast<int32_t>(T >= 128 ? 1 : 128 / T);
+        p.L = static_cast<int32_t>(p.spb * T);
+        p.smem_pad = 1;
+        p.io = T >= 32 ? 0 : 1;
+    }
+    if (p.op != BPLG_OP_FFT || !plan_structurally_valid(p, BPLG_F32, n, nullptr) || p.io > 1)
+        return set_error(BPLG_ERR_INVALID_PLAN, "fft no-alloc: invalid plan (the pipelined io mode is not offered here)");
+    const void *func = fft_func(p.radix, dir, p.smem_layout, p.smem_pad, p.io, p.L);
+    if (!func) return set_error(BPLG_ERR_INVALID_PLAN, "fft no-alloc: plan has no kernel");
+    const int smem = fft_smem_bytes(p.radix, p.smem_layout, p.smem_pad, p.io, n, p.spb);
+    cudaFuncAttributes fa;
+    cudaError_t e = cudaFuncGetAttributes(&fa, func);
+    if (e != cudaSuccess) return cuda_error(e, "cudaFuncGetAttributes");
+    if (p.L > fa.maxThreadsPerBlock) return set_error(BPLG_ERR_INVALID_PLAN, "fft no-alloc: block too large for the kernel");
+    if (smem > fa.maxDynamicSharedSizeBytes) {
+        e = cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        if (e != cudaSuccess) return cuda_error(e, "cudaFuncSetAttribute(max dynamic smem)");
+    }
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const float2 *tw = nullptr;
+    int rc = noalloc_setup(s, &tw);
+    if (rc != BPLG_OK) return rc;
+    int logn = ilog2(n);
+    int spb = p.spb;
+    const int64_t blocks = (batch + spb - 1) / spb;
+    void *args[] = {(void *)&in, (void *)&out, (void *)&tw, &logn, &spb, &batch};
+    e = cudaLaunchKernel(func, dim3(static_cast<unsigned>(blocks)), dim3(p.L), args, static_cast<size_t>(smem), s);
+    return e == cudaSuccess ? BPLG_OK : cuda_error(e, "fft no-alloc launch");
+}
