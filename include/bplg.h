@@ -189,6 +189,43 @@ int bplg_tridiag_refined(const float *a, const float *b, const float *c, const f
                          int64_t n, int64_t batch, int32_t max_iter, double tol, int32_t *iters,
                          const bplg_plan *plan, void *stream);
 
+/* ------------------------------------------------ uneven-size batches */
+
+/* One problem of an uneven batch (the uniform batches of Section IV-A
+ * generalised to mixed operations and sizes); every problem has its own
+ * device buffers, 16-byte aligned, laid out as in the batched calls. */
+typedef struct {
+    int32_t op;        /* BPLG_OP_SCAN, BPLG_OP_FFT or BPLG_OP_TRIDIAG */
+    int32_t n;         /* power of two, 32 <= n <= 8192 */
+    int32_t dtype;     /* scan: BPLG_I32 or BPLG_F32 */
+    int32_t dir;       /* FFT: -1 forward, +1 inverse (unnormalised) */
+    const void *in[4]; /* scan, FFT: in[0]; tridiag: a, b, c, d (float32) */
+    void *out;         /* scan, FFT: output (may equal in[0]); tridiag: x (may alias d) */
+} bplg_item;
+
+typedef struct bplg_uneven_batch *bplg_uneven_handle;
+
+/* Prepare an uneven batch on the current device: validate the items, group
+ * them by (operation, size) into units (largest first), copy the descriptors
+ * to library-owned device memory, and capture into a CUDA graph one counter
+ * reset plus three persistent kernels (scan, FFT, tridiag) that pull units
+ * from an atomic counter each.  The item buffers must stay valid while the
+ * handle is used.  Synchronous; allocates.
+ * Errors: INVALID_ARG, UNSUPPORTED_SIZE, CUDA. */
+int bplg_uneven_create(const bplg_item *items, int64_t count, bplg_uneven_handle *out);
+
+/* Run every problem of the batch: one graph launch on `stream`.  Launches of
+ * the same handle share its work counters, so they must not overlap on the
+ * GPU (launches on one stream never do).  Errors: INVALID_ARG, CUDA. */
+int bplg_uneven_launch(bplg_uneven_handle h, void *stream);
+
+/* Units per operation (scan, FFT, tridiag) of a prepared batch. */
+int bplg_uneven_units(bplg_uneven_handle h, int32_t *units_scan_fft_tridiag);
+
+/* Release the handle (graph and device descriptors).  Call after its last
+ * launch has completed. */
+int bplg_uneven_destroy(bplg_uneven_handle h);
+
 /* ------------------------------------------------------------- tuning */
 
 /* Per-SM limits that bound occupancy (Section IV-A: W^max, B^max, registers

@@ -34,7 +34,8 @@ TC_BF16, TC_F16 = 0, 1
 
 EXPORTED = [
     "bplg_scan_batched", "bplg_fft_batched", "bplg_fft_batched_noalloc", "bplg_tridiag_batched",
-    "bplg_tridiag_refined",
+    "bplg_tridiag_refined", "bplg_uneven_create", "bplg_uneven_launch", "bplg_uneven_units",
+    "bplg_uneven_destroy",
     "bplg_arch_query", "bplg_arch_preset", "bplg_occupancy", "bplg_guideline_select", "bplg_phi",
     "bplg_enumerate_plans", "bplg_plan_resources", "bplg_tune_plan", "bplg_tune_plans_cost",
     "bplg_query_plan", "bplg_time_plan", "bplg_check_plan", "bplg_device_status", "bplg_last_error",
@@ -79,6 +80,11 @@ class TuneReport(ctypes.Structure):
                 ("invalid", ctypes.c_int32), ("chosen_ms", ctypes.c_double), ("best_seen_ms", ctypes.c_double)]
 
 
+class Item(ctypes.Structure):
+    _fields_ = [("op", ctypes.c_int32), ("n", ctypes.c_int32), ("dtype", ctypes.c_int32), ("dir", ctypes.c_int32),
+                ("in_", ctypes.c_void_p * 4), ("out", ctypes.c_void_p)]
+
+
 COST_FN = ctypes.CFUNCTYPE(ctypes.c_double, ctypes.POINTER(Plan), ctypes.c_void_p)
 
 
@@ -95,6 +101,10 @@ def _load():
         "bplg_fft_batched_noalloc": ([P, P, I64, I64, I32_, PP, P], ctypes.c_int),
         "bplg_tridiag_batched": ([P, P, P, P, P, I64, I64, PP, P], ctypes.c_int),
         "bplg_tridiag_refined": ([P, P, P, P, P, I64, I64, I32_, D, P, PP, P], ctypes.c_int),
+        "bplg_uneven_create": ([ctypes.POINTER(Item), I64, ctypes.POINTER(ctypes.c_void_p)], ctypes.c_int),
+        "bplg_uneven_launch": ([ctypes.c_void_p, P], ctypes.c_int),
+        "bplg_uneven_units": ([ctypes.c_void_p, ctypes.POINTER(I32_)], ctypes.c_int),
+        "bplg_uneven_destroy": ([ctypes.c_void_p], ctypes.c_int),
         "bplg_arch_query": ([I32_, ctypes.POINTER(Arch)], ctypes.c_int),
         "bplg_arch_preset": ([I32_, ctypes.POINTER(Arch)], ctypes.c_int),
         "bplg_occupancy": ([ctypes.POINTER(Arch), I32_, I32_, I32_, ctypes.POINTER(I32_), ctypes.POINTER(I32_)],
@@ -196,6 +206,49 @@ def tridiag_refined(a, b, c, d, x, n: int, batch: int, max_iter: int = 10, tol: 
     """Float64-residual refined solve; x is float64 (see bplg_tridiag_refined)."""
     _check(lib.bplg_tridiag_refined(_ptr(a), _ptr(b), _ptr(c), _ptr(d), _ptr(x), n, batch, max_iter, tol,
                                     _ptr(iters), _plan_ref(plan), _stream(stream)))
+
+
+class UnevenBatch:
+    """An uneven batch prepared once (bplg_uneven_create) and run with one
+    graph launch per call (bplg_uneven_launch).  `items` is a list of dicts
+    {op, n, in: [tensor, ...], out: tensor, dtype?, dir?}; the tensors must
+    outlive the batch (they are kept referenced here)."""
+
+    def __init__(self, items):
+        arr = (Item * len(items))()
+        self._keep = []
+        for k, it in enumerate(items):
+            e = arr[k]
+            e.op, e.n = it["op"], it["n"]
+            e.dtype = it.get("dtype", I32)
+            e.dir = it.get("dir", -1)
+            for q, t in enumerate(it["in"]):
+                e.in_[q] = _ptr(t)
+                self._keep.append(t)
+            e.out = _ptr(it["out"])
+            self._keep.append(it["out"])
+        h = ctypes.c_void_p()
+        _check(lib.bplg_uneven_create(arr, len(items), ctypes.byref(h)))
+        self.handle = h
+
+    def launch(self, stream=None) -> None:
+        _check(lib.bplg_uneven_launch(self.handle, _stream(stream)))
+
+    def units(self):
+        u = (ctypes.c_int32 * 3)()
+        _check(lib.bplg_uneven_units(self.handle, u))
+        return tuple(u)
+
+    def close(self) -> None:
+        if self.handle:
+            lib.bplg_uneven_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 # -------------------------------------------------------------------- tuning

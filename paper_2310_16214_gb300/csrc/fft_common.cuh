@@ -1,0 +1,144 @@
+// Device building blocks of the Stockham FFT shared by the batched and the
+// uneven-batch kernels: radix-2/4/8/16 DFT codelets with compile-time
+// constants, the mixed-radix first stage, the Stockham output index map, and
+// the padded shared-memory index.
+#pragma once
+
+#include <cuda_runtime.h>
+
+namespace bplg {
+
+// cos and sin of 2 pi k / 16, k = 0..4 (the other eighths follow by symmetry)
+__host__ __device__ constexpr float cos16(int k) {
+    switch (k & 15) {
+        case 0: return 1.0f;
+        case 1: return 0.92387953251128675613f;
+        case 2: return 0.70710678118654752440f;
+        case 3: return 0.38268343236508977173f;
+        case 4: return 0.0f;
+        case 5: return -0.38268343236508977173f;
+        case 6: return -0.70710678118654752440f;
+        case 7: return -0.92387953251128675613f;
+        case 8: return -1.0f;
+        case 9: return -0.92387953251128675613f;
+        case 10: return -0.70710678118654752440f;
+        case 11: return -0.38268343236508977173f;
+        case 12: return 0.0f;
+        case 13: return 0.38268343236508977173f;
+        case 14: return 0.70710678118654752440f;
+        default: return 0.92387953251128675613f;
+    }
+}
+__host__ __device__ constexpr float sin16(int k) { return cos16(k - 4); }
+
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ float2 cmul(float2 a, float2 w) {
+    return make_float2(a.x * w.x - a.y * w.y, a.x * w.y + a.y * w.x);
+}
+
+// a * exp(DIR 2 pi i k / m) for compile-time k, m in {2, 4, 8, 16}
+template <int DIR, int K, int M>
+__device__ __forceinline__ float2 cmul_root(float2 a) {
+    constexpr int k16 = (K * (16 / M)) & 15;
+    if constexpr (k16 == 0) {
+        return a;
+    } else if constexpr (k16 == 8) {
+        return make_float2(-a.x, -a.y);
+    } else if constexpr (k16 == 4) {  // w = DIR * i
+        return DIR < 0 ? make_float2(a.y, -a.x) : make_float2(-a.y, a.x);
+    } else if constexpr (k16 == 12) {  // w = -DIR * i
+        return DIR < 0 ? make_float2(-a.y, a.x) : make_float2(a.y, -a.x);
+    } else {
+        constexpr float c = cos16(k16);
+        constexpr float s = DIR * sin16(k16);
+        return make_float2(a.x * c - a.y * s, a.x * s + a.y * c);
+    }
+}
+
+__host__ __device__ constexpr int bitrev(int i, int bits) {
+    int r = 0;
+    for (int b = 0; b < bits; ++b) r |= ((i >> b) & 1) << (bits - 1 - b);
+    return r;
+}
+__host__ __device__ constexpr int clog2(int v) { return v <= 1 ? 0 : 1 + clog2(v / 2); }
+
+// One radix-2 decimation-in-frequency layer of half-size H on R registers:
+// (a, b) -> (a + b, (a - b) W_{2H}^k).
+template <int R, int DIR, int H, int B0, int K>
+__device__ __forceinline__ void dif_bfly(float2 (&v)[R]) {
+    if constexpr (B0 < R) {
+        if constexpr (K < H) {
+            float2 a = v[B0 + K], b = v[B0 + K + H];
+            v[B0 + K] = cadd(a, b);
+            v[B0 + K + H] = cmul_root<DIR, K, 2 * H>(csub(a, b));
+            dif_bfly<R, DIR, H, B0, K + 1>(v);
+        } else {
+            dif_bfly<R, DIR, H, B0 + 2 * H, 0>(v);
+        }
+    }
+}
+template <int R, int DIR, int H>
+__device__ __forceinline__ void dif_layers(float2 (&v)[R]) {
+    if constexpr (H >= 1) {
+        dif_bfly<R, DIR, H, 0, 0>(v);
+        dif_layers<R, DIR, H / 2>(v);
+    }
+}
+
+// In-register R-point DFT, natural order in and out.
+template <int R, int DIR>
+__device__ __forceinline__ void dft_codelet(float2 (&v)[R]) {
+    if constexpr (R > 1) {
+        dif_layers<R, DIR, R / 2>(v);
+        float2 t[R];
+#pragma unroll
+        for (int i = 0; i < R; ++i) t[i] = v[bitrev(i, clog2(R))];
+#pragma unroll
+        for (int i = 0; i < R; ++i) v[i] = t[i];
+    }
+}
+
+// First stage with the lower radix R0 (Ns = 1, no twiddles): the thread's R
+// registers hold R/R0 butterflies, butterfly q using registers q, q+Q, ...
+template <int R, int R0, int DIR>
+__device__ __forceinline__ void first_stage_mixed(float2 (&v)[R]) {
+    constexpr int Q = R / R0;
+#pragma unroll
+    for (int q = 0; q < Q; ++q) {
+        float2 u[R0];
+#pragma unroll
+        for (int r = 0; r < R0; ++r) u[r] = v[q + r * Q];
+        dft_codelet<R0, DIR>(u);
+#pragma unroll
+        for (int r = 0; r < R0; ++r) v[q + r * Q] = u[r];
+    }
+}
+
+// Output position of register m after a stage.  Radix-R stage: base + m Ns.
+// Mixed first stage of radix R0 = 2^lr0 (Q = R / R0 butterflies per thread):
+// register m = q + r Q holds output r of butterfly j + q T, i.e. position
+// (j + q T) R0 + r.
+struct OutMap {
+    int base, shift, mixed, lr0, lq, j, T;
+    __device__ __forceinline__ int operator()(int m) const {
+        if (mixed) return ((j + (m & ((1 << lq) - 1)) * T) << lr0) + (m >> lq);
+        return base + (m << shift);
+    }
+};
+
+template <int LAYOUT, int PAD>
+__device__ __forceinline__ int pidx(int e) {
+    if constexpr (!PAD) return e;
+    if constexpr (LAYOUT == 0) return e + (e >> 4);
+    return e + (e >> 5);
+}
+
+template <int LAYOUT, int PAD>
+__host__ __device__ __forceinline__ int sig_stride(int n) {
+    if (!PAD) return n;
+    int p = LAYOUT == 0 ? (n >> 4) : (n >> 5);
+    return n + (p > 0 ? p : 1);
+}
+
+}  // namespace bplg
