@@ -30,6 +30,7 @@ from __future__ import annotations
 
 import argparse
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -568,6 +569,59 @@ def tune_report(args):
     print(json.dumps({"tune_report": summary}))
 
 
+def precision_report(args):
+    """Precision configuration: FFT N in {2^10, 2^12, 2^14}, batch 2^26/N,
+    tensor-core radix-16 stages with BF16 and FP16 split operands against
+    the float32 CUDA-core Stockham path; error against the float64 oracle on
+    sampled signals (max and median relative L2) and the median time of
+    `reps` launches (plans: learned tuner for each path)."""
+    import torch
+    torch.cuda.set_device(0)
+    import oracle
+    import paper_2310_16214_gb300 as bp
+    peak, _ = read_peaks()
+    out = []
+    for n in (1 << 10, 1 << 12, 1 << 14):
+        batch = (1 << 26) // n
+        z = si.fft_c64(batch, n, seed=si.CONFIG_SEEDS["precision"], stream=n)
+        zd = torch.from_numpy(z.view(np.float32).reshape(-1)).cuda()
+        od = torch.empty_like(zd)
+        rng = np.random.default_rng(3)
+        rows = np.unique(rng.integers(0, batch, 64))
+        ref = oracle.fft(z[rows], -1)
+        st = torch.cuda.current_stream()
+        paths = {
+            "fp32": (bp.OP_FFT, lambda p: bp.fft_batched(zd, od, n, batch, -1, plan=p)),
+            "tc_bf16": (bp.OP_FFT_TC, lambda p: bp.fft_tc_batched(zd, od, n, batch, -1, bp.TC_BF16, plan=p)),
+            "tc_f16": (bp.OP_FFT_TC, lambda p: bp.fft_tc_batched(zd, od, n, batch, -1, bp.TC_F16, plan=p)),
+        }
+        row = {"n": n, "batch": batch}
+        for name, (op, fn) in paths.items():
+            p, rep = bp.tune_plan(op, bp.F32, n, batch, bp.TUNE_LEARNED, budget=40, seed=args.seed)
+            for _ in range(3):
+                fn(p)
+            ts = []
+            for _ in range(args.reps):
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(st)
+                fn(p)
+                e1.record(st)
+                ts.append((e0, e1))
+            torch.cuda.synchronize()
+            ms = statistics.median(a.elapsed_time(b) for a, b in ts)
+            X = od.cpu().numpy().view(np.complex64).reshape(batch, n)[rows].astype(np.complex128)
+            err = np.linalg.norm(X - ref, axis=1) / np.linalg.norm(ref, axis=1)
+            row[name] = {"ms": round(ms, 5), "gelem_s": round(n * batch / (ms * 1e-3) / 1e9, 1),
+                         "hbm_frac": round(16 * n * batch / (ms * 1e-3) / 1e9 / peak, 4),
+                         "err_max": float("%.3e" % err.max()), "err_median": float("%.3e" % np.median(err)),
+                         "tolerance": 1e-5 * math.log2(n), "plan": {k: v for k, v in p.as_dict().items()
+                                                                    if k in ("P", "L", "spb", "smem_layout", "io")}}
+        out.append(row)
+        print(json.dumps(row), flush=True)
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -579,6 +633,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--tune-report", action="store_true", help="tuned vs exhaustive Phi report instead of the bench")
+    ap.add_argument("--precision-report", action="store_true",
+                    help="tensor-core (BF16/FP16 split) vs float32 FFT: error and time per N")
     ap.add_argument("--ops", default="", help="comma-separated ops for --tune-report")
     ap.add_argument("--reps", type=int, default=50)
     ap.add_argument("--bo-budget", type=int, default=40)
@@ -591,6 +647,8 @@ def main():
     args = ap.parse_args()
     if args.tune_report:
         tune_report(args)
+    elif args.precision_report:
+        precision_report(args)
     elif args.impl == "reference":
         run_reference(args)
     else:

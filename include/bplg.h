@@ -136,6 +136,22 @@ int bplg_scan_batched(int32_t dtype, const void *in, void *out, int64_t n, int64
 int bplg_fft_batched(const void *in, void *out, int64_t n, int64_t batch, int32_t dir,
                      const bplg_plan *plan, void *stream);
 
+/* The same FFT with every radix-16 Stockham stage run on tensor cores: each
+ * 16-point DFT of a stage is a 32 x 32 real contraction (mma.sync
+ * m16n8k16) on 16-bit operands split into hi and lo parts, x = xh + xl and
+ * F = Fh + Fl, summing xh Fh + xh Fl + xl Fh in float32; twiddles are
+ * applied in float32 from the float64-generated table, and a mixed-radix
+ * first stage (log2 n not a multiple of 4) runs on the CUDA cores.  Not in
+ * the paper (whose FFT is float32 on CUDA cores, Section III); the error
+ * against the float64 oracle is reported per size.
+ *   precision BPLG_TC_BF16 or BPLG_TC_F16 (FP16 scales each stage by 1/4,
+ *             exactly, and undoes it at the end).
+ *   n        power of two, 512 <= n <= 16384; in, out as bplg_fft_batched.
+ *   plan     op BPLG_OP_FFT_TC (P = radix = 16, spb), or NULL.
+ * Errors: INVALID_ARG, UNSUPPORTED_SIZE, INVALID_PLAN, CUDA. */
+int bplg_fft_tc_batched(const void *in, void *out, int64_t n, int64_t batch, int32_t dir,
+                        int32_t precision, const bplg_plan *plan, void *stream);
+
 /* The FFT of bplg_fft_batched for callers that cannot allocate device
  * memory while they run -- code under an allocator that owns the whole
  * device, fixed real-time memory budgets, code that must not trigger the

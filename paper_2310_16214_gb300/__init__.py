@@ -33,7 +33,8 @@ TUNE_ANALYTIC, TUNE_LEARNED, TUNE_EXHAUSTIVE = 0, 1, 2
 TC_BF16, TC_F16 = 0, 1
 
 EXPORTED = [
-    "bplg_scan_batched", "bplg_fft_batched", "bplg_fft_batched_noalloc", "bplg_tridiag_batched",
+    "bplg_scan_batched", "bplg_fft_batched", "bplg_fft_tc_batched", "bplg_fft_batched_noalloc",
+    "bplg_tridiag_batched",
     "bplg_tridiag_refined", "bplg_uneven_create", "bplg_uneven_launch", "bplg_uneven_units",
     "bplg_uneven_destroy",
     "bplg_arch_query", "bplg_arch_preset", "bplg_occupancy", "bplg_guideline_select", "bplg_phi",
@@ -99,6 +100,7 @@ def _load():
         "bplg_scan_batched": ([I32_, P, P, I64, I64, PP, P], ctypes.c_int),
         "bplg_fft_batched": ([P, P, I64, I64, I32_, PP, P], ctypes.c_int),
         "bplg_fft_batched_noalloc": ([P, P, I64, I64, I32_, PP, P], ctypes.c_int),
+        "bplg_fft_tc_batched": ([P, P, I64, I64, I32_, I32_, PP, P], ctypes.c_int),
         "bplg_tridiag_batched": ([P, P, P, P, P, I64, I64, PP, P], ctypes.c_int),
         "bplg_tridiag_refined": ([P, P, P, P, P, I64, I64, I32_, D, P, PP, P], ctypes.c_int),
         "bplg_uneven_create": ([ctypes.POINTER(Item), I64, ctypes.POINTER(ctypes.c_void_p)], ctypes.c_int),
@@ -186,6 +188,13 @@ def scan_batched(inp, out, n: int, batch: int, dtype: Optional[int] = None, plan
 def fft_batched(inp, out, n: int, batch: int, direction: int = -1, plan: Optional[Plan] = None, stream=None) -> None:
     """Complex Stockham FFT of [batch][n] complex64 (see bplg_fft_batched)."""
     _check(lib.bplg_fft_batched(_ptr(inp), _ptr(out), n, batch, direction, _plan_ref(plan), _stream(stream)))
+
+
+def fft_tc_batched(inp, out, n: int, batch: int, direction: int = -1, precision: int = TC_BF16,
+                   plan: Optional[Plan] = None, stream=None) -> None:
+    """FFT with tensor-core radix-16 stages, split hi/lo operands (see bplg_fft_tc_batched)."""
+    _check(lib.bplg_fft_tc_batched(_ptr(inp), _ptr(out), n, batch, direction, precision, _plan_ref(plan),
+                                   _stream(stream)))
 
 
 def fft_batched_noalloc(inp, out, n: int, batch: int, direction: int = -1, plan: Optional[Plan] = None,

@@ -109,6 +109,23 @@ int bplg_fft_batched(const void *in, void *out, int64_t n, int64_t batch, int32_
     return fft_launch(p, in, out, n, batch, dir, static_cast<cudaStream_t>(stream));
 }
 
+int bplg_fft_tc_batched(const void *in, void *out, int64_t n, int64_t batch, int32_t dir, int32_t precision,
+                        const bplg_plan *plan, void *stream) {
+    clear_error();
+    if (!in || !out) return set_error(BPLG_ERR_INVALID_ARG, "fft tc: null buffer");
+    if (n < 1 || batch < 1) return set_error(BPLG_ERR_INVALID_ARG, "fft tc: n and batch must be >= 1");
+    if (dir != -1 && dir != 1) return set_error(BPLG_ERR_INVALID_ARG, "fft tc: dir must be -1 or +1");
+    if (precision != BPLG_TC_BF16 && precision != BPLG_TC_F16)
+        return set_error(BPLG_ERR_INVALID_ARG, "fft tc: precision must be BPLG_TC_BF16 or BPLG_TC_F16");
+    if (!size_ok(BPLG_OP_FFT_TC, n, 512))
+        return set_error(BPLG_ERR_UNSUPPORTED_SIZE, "fft tc: n must be a power of two in [512, 16384]");
+    if (!aligned16(in) || !aligned16(out)) return set_error(BPLG_ERR_INVALID_ARG, "fft tc: buffers must be 16-byte aligned");
+    bplg_plan p;
+    int rc = resolve_plan(BPLG_OP_FFT_TC, BPLG_F32, n, batch, plan, &p);
+    if (rc != BPLG_OK) return rc;
+    return fft_tc_launch(p, in, out, n, batch, dir, precision, static_cast<cudaStream_t>(stream));
+}
+
 int bplg_tridiag_batched(const float *a, const float *b, const float *c, const float *d, float *x, int64_t n,
                          int64_t batch, const bplg_plan *plan, void *stream) {
     clear_error();
@@ -220,7 +237,8 @@ int bplg_tune_plan(int32_t op, int32_t dtype, int64_t n, int64_t batch, int32_t 
     if (max_log_for(op) < 0) return set_error(BPLG_ERR_INVALID_ARG, "unknown op");
     if (batch < 1) return set_error(BPLG_ERR_INVALID_ARG, "batch must be >= 1");
     if (method < BPLG_TUNE_ANALYTIC || method > BPLG_TUNE_EXHAUSTIVE) return set_error(BPLG_ERR_INVALID_ARG, "unknown method");
-    if (!size_ok(op, n, op == BPLG_OP_SCAN ? 1 : 2)) return set_error(BPLG_ERR_UNSUPPORTED_SIZE, "unsupported size");
+    if (!size_ok(op, n, op == BPLG_OP_SCAN ? 1 : (op == BPLG_OP_FFT_TC ? 512 : 2)))
+        return set_error(BPLG_ERR_UNSUPPORTED_SIZE, "unsupported size");
     return tune_on_device(op, dtype, n, batch, method, budget, seed, out, report);
 }
 
@@ -252,7 +270,8 @@ int bplg_query_plan(int32_t op, int32_t dtype, int64_t n, int64_t batch, bplg_pl
     if (!out) return set_error(BPLG_ERR_INVALID_ARG, "null output");
     if (max_log_for(op) < 0) return set_error(BPLG_ERR_INVALID_ARG, "unknown op");
     if (batch < 1) return set_error(BPLG_ERR_INVALID_ARG, "batch must be >= 1");
-    if (!size_ok(op, n, op == BPLG_OP_SCAN ? 1 : 2)) return set_error(BPLG_ERR_UNSUPPORTED_SIZE, "unsupported size");
+    if (!size_ok(op, n, op == BPLG_OP_SCAN ? 1 : (op == BPLG_OP_FFT_TC ? 512 : 2)))
+        return set_error(BPLG_ERR_UNSUPPORTED_SIZE, "unsupported size");
     return resolve_plan(op, dtype, n, batch, nullptr, out);
 }
 

@@ -49,6 +49,9 @@ bool fft_launch_info(const bplg_plan &p, int64_t n, int64_t batch, int dir, Laun
 int fft_launch(const bplg_plan &p, const void *in, void *out, int64_t n, int64_t batch, int dir,
                cudaStream_t s);
 
+int fft_tc_launch(const bplg_plan &p, const void *in, void *out, int64_t n, int64_t batch, int dir, int prec,
+                  cudaStream_t s);
+
 bool tridiag_launch_info(const bplg_plan &p, int64_t n, int64_t batch, bool refined, Launch *out);
 int tridiag_launch(const bplg_plan &p, const float *a, const float *b, const float *c,
                    const float *d, float *x, int64_t n, int64_t batch, cudaStream_t s);

@@ -17,6 +17,8 @@
 namespace bplg {
 
 int fft_smem_bytes(int radix, int layout, int pad, int io, int64_t n, int spb);
+int fft_tc_smem_bytes(int64_t n, int spb);
+bool fft_tc_launch_info(const bplg_plan &p, int64_t n, int64_t batch, int prec, int dir, Launch *out);
 int tridiag_smem_bytes(int pad, int64_t n, int spb, bool refined, int layout, int io, int log_m, int P);
 
 namespace {
@@ -65,6 +67,7 @@ int max_log_for(int op) {
         case BPLG_OP_FFT: return kFftMaxLog;
         case BPLG_OP_TRIDIAG: return kTridiagMaxLog;
         case BPLG_OP_TRIDIAG_REFINED: return kRefinedMaxLog;
+        case BPLG_OP_FFT_TC: return kFftMaxLog;
         default: return -1;
     }
 }
@@ -93,6 +96,12 @@ bool plan_structurally_valid(const bplg_plan &p, int dtype, int64_t n, std::stri
             if (p.smem_layout < 0 || p.smem_layout > 1 || p.smem_pad < 0 || p.smem_pad > 1 || p.io < 0 || p.io > 2)
                 return fail(why, "FFT: layout/pad/io out of range");
             if (p.smem_layout == 1 && p.io != 0) return fail(why, "FFT: staged and pipelined io need the interleaved layout");
+            return true;
+        case BPLG_OP_FFT_TC:
+            if (p.radix != 16 || p.P != 16) return fail(why, "tensor-core FFT: radix and P are 16");
+            if (n < 512) return fail(why, "tensor-core FFT: n >= 512 (a warp per 32 butterflies)");
+            if (p.smem_pad != 1 || p.smem_layout != 0 || p.io != 1)
+                return fail(why, "tensor-core FFT: padded interleaved layout, staged io");
             return true;
         case BPLG_OP_TRIDIAG:
         case BPLG_OP_TRIDIAG_REFINED: {
@@ -128,6 +137,7 @@ int plan_smem_bytes(const bplg_plan &p, int dtype, int64_t n) {
     switch (p.op) {
         case BPLG_OP_SCAN: return 0;
         case BPLG_OP_FFT: return fft_smem_bytes(p.radix, p.smem_layout, p.smem_pad, p.io, n, p.spb);
+        case BPLG_OP_FFT_TC: return fft_tc_smem_bytes(n, p.spb);
         case BPLG_OP_TRIDIAG:
             return tridiag_smem_bytes(p.smem_pad, n, p.spb, false, p.smem_layout, p.io, ilog2(p.cr_switch), p.P);
         case BPLG_OP_TRIDIAG_REFINED:
@@ -152,6 +162,12 @@ void plan_finalize(bplg_plan *p, int dtype, int64_t n) {
             p->shuffle = 0;
             p->pattern = p->cr_switch = 0;
             p->S = plan_smem_bytes(*p, dtype, n) > 0 ? static_cast<int32_t>(p->spb * n) : 0;
+            break;
+        case BPLG_OP_FFT_TC:
+            p->radix = p->P;
+            p->shuffle = p->pattern = p->cr_switch = p->smem_layout = 0;
+            p->smem_pad = p->io = 1;
+            p->S = static_cast<int32_t>(p->spb * n);
             break;
         case BPLG_OP_TRIDIAG:
         case BPLG_OP_TRIDIAG_REFINED:
@@ -190,6 +206,10 @@ std::vector<bplg_plan> enumerate_structural(int op, int dtype, int64_t n) {
                     p.pattern = pat;
                     push(p);
                 }
+            } else if (op == BPLG_OP_FFT_TC) {
+                if (P != 16) continue;
+                p.radix = 16;
+                push(p);
             } else if (op == BPLG_OP_FFT) {
                 if (P < 2 || P > 16) continue;
                 p.radix = P;
@@ -291,6 +311,7 @@ bool launch_info_for(const bplg_plan &p, int dtype, int64_t n, Launch *li) {
         case BPLG_OP_FFT: return fft_launch_info(p, n, 1, -1, li);
         case BPLG_OP_TRIDIAG: return tridiag_launch_info(p, n, 1, false, li);
         case BPLG_OP_TRIDIAG_REFINED: return tridiag_launch_info(p, n, 1, true, li);
+        case BPLG_OP_FFT_TC: return fft_tc_launch_info(p, n, 1, BPLG_TC_BF16, -1, li);
         default: return false;
     }
 }

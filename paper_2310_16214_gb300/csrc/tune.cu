@@ -544,7 +544,7 @@ __global__ void fill_kernel(int op, int dtype, int64_t n, int64_t total, void *p
                 static_cast<int32_t *>(p0)[i] = static_cast<int32_t>(u * 1000.0f);
             else
                 static_cast<float *>(p0)[i] = u;
-        } else if (op == BPLG_OP_FFT) {
+        } else if (op == BPLG_OP_FFT || op == BPLG_OP_FFT_TC) {
             static_cast<float2 *>(p0)[i] = make_float2(u, -u * 0.5f);
         } else {
             static_cast<float *>(p0)[i] = (i % n) ? 0.5f * u : 0.f;
@@ -570,6 +570,7 @@ int launch_plan(const bplg_plan &p, int dtype, int64_t n, int64_t batch, void *i
     switch (p.op) {
         case BPLG_OP_SCAN: return scan_launch(p, dtype, in, out, n, batch, s);
         case BPLG_OP_FFT: return fft_launch(p, in, out, n, batch, -1, s);
+        case BPLG_OP_FFT_TC: return fft_tc_launch(p, in, out, n, batch, -1, BPLG_TC_BF16, s);
         case BPLG_OP_TRIDIAG:
             return tridiag_launch(p, static_cast<const float *>(in), static_cast<const float *>(b),
                                   static_cast<const float *>(c), static_cast<const float *>(d),
@@ -645,8 +646,9 @@ struct TimingArena {
         batch = batch_;
         cudaError_t e;
         const int64_t total = n * batch;
-        const size_t esz = op == BPLG_OP_FFT ? 8 : 4;
-        const size_t osz = (op == BPLG_OP_FFT || op == BPLG_OP_TRIDIAG_REFINED) ? 8 : 4;
+        const bool cplx = op == BPLG_OP_FFT || op == BPLG_OP_FFT_TC;
+        const size_t esz = cplx ? 8 : 4;
+        const size_t osz = (cplx || op == BPLG_OP_TRIDIAG_REFINED) ? 8 : 4;
         if ((e = cudaMalloc(&tb.in, total * esz)) != cudaSuccess) return cuda_error(e, "timing buffers");
         if ((e = cudaMalloc(&tb.out, total * osz)) != cudaSuccess) return cuda_error(e, "timing buffers");
         if (op == BPLG_OP_TRIDIAG || op == BPLG_OP_TRIDIAG_REFINED) {

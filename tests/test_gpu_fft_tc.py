@@ -1,0 +1,68 @@
+"""Tensor-core FFT (radix-16 stages as split hi/lo BF16 or FP16 MMA with
+float32 accumulation) against the float64 oracle: relative L2 error per
+signal <= 1e-5 * log2 N, forward and inverse, every plan, both precisions."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import seeded_inputs as si
+from tests.gpu_util import c64_from_dev, c64_to_dev, fft_rel_err, sample_rows
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def bp():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2310_16214_gb300 as bp
+    return bp
+
+
+def run(bp, z, direction, prec, plan=None):
+    batch, n = z.shape
+    zd = c64_to_dev(z)
+    out = torch.empty_like(zd)
+    bp.fft_tc_batched(zd, out, n, batch, direction, precision=prec, plan=plan)
+    torch.cuda.synchronize()
+    return c64_from_dev(out)
+
+
+@pytest.mark.parametrize("n", [512, 1024, 2048, 4096, 8192, 16384])
+@pytest.mark.parametrize("prec", [0, 1])
+def test_every_plan(bp, n, prec):
+    batch = 5
+    z = si.fft_c64(batch, n, stream=600 + n)
+    refs = {d: oracle.fft(z, d) for d in (-1, 1)}
+    plans = bp.enumerate_plans(bp.OP_FFT_TC, bp.F32, n)
+    assert plans
+    for p in plans:
+        for d in (-1, 1):
+            err = fft_rel_err(run(bp, z, d, prec, p), refs[d]).max()
+            assert err <= 1e-5 * math.log2(n), (p, d, prec, err)
+
+
+@pytest.mark.parametrize("n", [1024, 4096, 16384])
+def test_precision_configuration_sampled(bp, n):
+    # batch = 2^26 / N signals, default plan, both precisions
+    batch = (1 << 26) // n
+    z = si.fft_c64(batch, n, seed=si.CONFIG_SEEDS["precision"], stream=n)
+    rows = sample_rows(batch, k=24)
+    ref = oracle.fft(z[rows], -1)
+    for prec in (0, 1):
+        X = run(bp, z, -1, prec)
+        assert fft_rel_err(X[rows], ref).max() <= 1e-5 * math.log2(n)
+
+
+def test_argument_errors(bp):
+    z = torch.zeros(2 * 1024, dtype=torch.float32, device="cuda")
+    with pytest.raises(bp.BplgError) as e:
+        bp.fft_tc_batched(z, z, 256, 1)
+    assert e.value.code == bp.ERR_UNSUPPORTED_SIZE
+    with pytest.raises(bp.BplgError) as e:
+        bp.fft_tc_batched(z, z, 1024, 1, precision=7)
+    assert e.value.code == bp.ERR_INVALID_ARG
