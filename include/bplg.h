@@ -87,8 +87,11 @@ typedef enum { BPLG_TC_BF16 = 0, BPLG_TC_F16 = 1 } bplg_tc_precision;
  *           Tridiag: 0 all CR levels in place in shared memory, 1 one
  *           shared-memory array per CR level (stride-free), 2 the first
  *           log2 P CR levels in registers, the rest in shared memory.
- *           Refined tridiag: bit 0 coefficients also cached as float64 in
- *           shared memory, bit 1 one shared-memory array per CR level.
+ *           Refined tridiag: 0-3: shared-memory solver, bit 0 coefficients
+ *           also cached as float64, bit 1 one array per CR level; 4 every
+ *           equation in registers (register-level CR), 5 the same with the
+ *           coefficients held as float64 registers and their float32
+ *           copies in shared memory (P <= 8).
  *   smem_pad 1: pad shared-memory rows against bank conflicts.
  *   io      FFT: 0 registers <-> global memory directly, 1 staged through
  *           shared memory with 16-byte accesses, 2 persistent blocks fed by
@@ -195,7 +198,11 @@ int bplg_tridiag_batched(const float *a, const float *b, const float *c, const f
 /* The same solver inside iterative refinement: x0 = solve32(d); then
  * r = d - A x_k in float64 from the stored float32 coefficients, a float32
  * solve of the power-of-two-scaled residual, and x_{k+1} = x_k + e in
- * float64; stop when max|e| <= tol * max|x| or after max_iter corrections.
+ * float64.  A system stops when the correction just applied has
+ * max|e| <= tol * max|x0|, or, before another solve, when its residual
+ * bounds the error: for strictly diagonally dominant rows
+ * max|r| / min_i(|b_i| - |a_i| - |c_i|) <= tol * max|x0|; and after at most
+ * max_iter corrections.
  *   x       device, float64 [batch][n] (must not alias the inputs).
  *   iters   device int32 [batch] (corrections applied per system) or NULL.
  *   n       power of two, 2 <= n <= 4096.

@@ -24,10 +24,14 @@
 // the hardware reciprocal (about 1 ulp), well inside the float32 tolerance.
 //
 // The refined variant keeps the original coefficients beside a working copy
-// and x in float64; each correction computes r = d - A x in float64 from the
+// and x in float64; each iteration computes r = d - A x in float64 from the
 // stored float32 coefficients, scales r by a power of two sigma so that
 // max|r sigma| is in [1/2, 1), solves A e' = r sigma in float32 with the same
-// CR/PCR code, and adds e = e' / sigma to x in float64.  With smem_layout 1 the
+// CR/PCR code, and adds e = e' / sigma to x in float64.  A system stops when
+// the correction just applied is below tol max|x|, or -- before solving --
+// when its residual proves the error small: for a strictly diagonally
+// dominant A, ||A^-1||_inf <= 1/delta with delta = min_i |b_i| - |a_i| - |c_i|
+// (Varah's bound), so max|r| / delta <= tol max|x| bounds ||x - x*||.  With smem_layout 1 the
 // coefficients are also cached as float64 in shared memory, so the residual
 // needs no conversions (the float64 pipe is the bottleneck of this kernel).
 #include "device_util.cuh"
@@ -575,9 +579,19 @@ __global__ void __launch_bounds__(1024)
         xmaxf = fmaxf(xmaxf, fabsf(v));
     }
     xmaxf = system_max(xmaxf, red, wps);
+    // diagonal-dominance margin delta = min_i |b_i| - |a_i| - |c_i| (kept only
+    // if positive, slightly shrunk for its float32 rounding): then
+    // ||A^-1|| <= 1/delta and ||x - x*|| <= ||r|| / delta
+    float dmin = 3.0e38f;
+    for (int i = t; i < n; i += tps) {
+        const float4 q = o[i];
+        dmin = fminf(dmin, fabsf(q.y) - fabsf(q.x) - fabsf(q.z));
+    }
+    dmin = -system_max(-dmin, red, wps);
+    const double dmarg = dmin > 0.f ? static_cast<double>(dmin) * (1.0 - 1e-6) : 0.0;
 
     int applied = 0;
-    for (int k = 0; k < max_iter; ++k) {
+    for (int k = 0;; ++k) {
         // residual r = d - A x in float64 from the stored float32 coefficients
         float rmaxf = 0.f;
         for (int i = t; i < n; i += tps) {
@@ -600,6 +614,18 @@ __global__ void __launch_bounds__(1024)
             w[widx(i)] = make_float4(q.x, q.y, q.z, rf);
         }
         rmaxf = system_max(rmaxf, red, wps);
+        // the residual already bounds the error: stop before solving when
+        // max|r| / delta <= tol max|x|
+        if (t == 0 && dmarg > 0.0 &&
+            static_cast<double>(rmaxf) * (1.0 + 1e-6) <= tol * static_cast<double>(xmaxf) * dmarg)
+            done_sys[s] = 1;
+        __syncthreads();
+        {
+            int all_done = 1;
+            for (int q = 0; q < spb; ++q) all_done &= done_sys[q];
+            __syncthreads();
+            if (all_done || k == max_iter) break;
+        }
         // sigma = 2^-ex brings max|r sigma| into [1/2, 1); the exponent is
         // clamped so both powers of two stay normal
         int ex = 0;
@@ -637,11 +663,197 @@ __global__ void __launch_bounds__(1024)
     }
 }
 
+// Register-resident refinement (refined smem_layout 4 and 5).  Each thread
+// keeps its P equations' x in float64 and its working copy in registers; the
+// float32 correction solves are the register-level CR (the middle system and
+// boundary equations in shared memory), and the residual's neighbours across
+// threads come from two float64 slots per thread.  Layout 4 keeps the
+// original coefficients as float32 registers and widens them in every
+// residual; layout 5 keeps them as float64 registers (no conversion in the
+// residual -- on this GPU conversions occupy the float64 pipe) and their
+// float32 copies in shared memory for resetting the working copy.  The
+// arithmetic is that of the shared-memory refinement.
+template <int P, int COEF64, int PAD, int SHUFFLE, int MAXT>
+__global__ void __launch_bounds__(MAXT)
+    tridiag_refined_reg_kernel(const float *ga, const float *gb, const float *gc, const float *gd, double *x,
+                               int32_t *iters, int logn, int log_m, int log_tps, int spb, int64_t batch,
+                               int max_iter, double tol) {
+    constexpr int LP = (P >= 16) ? 4 : (P >= 8) ? 3 : (P >= 4) ? 2 : 1;
+    constexpr int PF = COEF64 ? 1 : P;  // float32 coefficient registers (layout 4)
+    constexpr int PD = COEF64 ? P : 1;  // float64 coefficient registers (layout 5)
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ float red[32];
+    __shared__ int done_sys[32];
+    const int n = 1 << logn;
+    const int tps = 1 << log_tps;
+    const int wps = tps >> 5;
+    const int tid = threadIdx.x;
+    const int s = tid >> log_tps;
+    const int t = tid & (tps - 1);
+    const int64_t sig0 = static_cast<int64_t>(blockIdx.x) * spb;
+    const int64_t left = batch - sig0;
+    const int nvalid = left < spb ? static_cast<int>(left) : spb;
+    const bool valid = s < nvalid;
+    const int mstride = tstride<PAD>(tps);
+    float4 *rows = reinterpret_cast<float4 *>(smem_raw) + s * mstride;
+    float4 *bnd = reinterpret_cast<float4 *>(smem_raw) + spb * mstride;
+    double *xfirst = reinterpret_cast<double *>(reinterpret_cast<float4 *>(smem_raw) + spb * mstride +
+                                                blockDim.x * LP);
+    double *xlast = xfirst + blockDim.x;
+    float4 *ocoef = reinterpret_cast<float4 *>(xlast + blockDim.x) + tid * P;  // layout 5: this thread's rows
+    const int64_t g = (sig0 + s) * n + static_cast<int64_t>(t) * P;
+
+    float la[P], lb[P], lc[P], ld[P];
+    if (valid) {
+        load_run<float, P>(ga + g, la);
+        load_run<float, P>(gb + g, lb);
+        load_run<float, P>(gc + g, lc);
+        load_run<float, P>(gd + g, ld);
+    } else {
+#pragma unroll
+        for (int i = 0; i < P; ++i) {
+            la[i] = 0.f;
+            lb[i] = 1.f;
+            lc[i] = 0.f;
+            ld[i] = 0.f;
+        }
+    }
+    if (t == 0) la[0] = 0.f;
+    if (t == tps - 1) lc[P - 1] = 0.f;
+    float oa[PF], ob[PF], oc[PF], od[PF];
+    double ca[PD], cb[PD], cc[PD], cd[PD];
+    float dmin = 3.0e38f;
+#pragma unroll
+    for (int i = 0; i < P; ++i) {
+        dmin = fminf(dmin, fabsf(lb[i]) - fabsf(la[i]) - fabsf(lc[i]));
+        if constexpr (COEF64) {
+            ca[i] = static_cast<double>(la[i]);
+            cb[i] = static_cast<double>(lb[i]);
+            cc[i] = static_cast<double>(lc[i]);
+            cd[i] = static_cast<double>(ld[i]);
+            ocoef[i] = make_float4(la[i], lb[i], lc[i], ld[i]);
+        } else {
+            oa[i] = la[i];
+            ob[i] = lb[i];
+            oc[i] = lc[i];
+            od[i] = ld[i];
+        }
+    }
+    // la..ld become the working copy
+    if (t == 0) done_sys[s] = valid ? 0 : 1;
+    cr_register_solve<P, PAD, SHUFFLE>(la, lb, lc, ld, log_m, log_tps, t, rows, bnd);
+    double xs[P];
+    float xmaxf = 0.f;
+#pragma unroll
+    for (int i = 0; i < P; ++i) {
+        xs[i] = static_cast<double>(ld[i]);
+        xmaxf = fmaxf(xmaxf, fabsf(ld[i]));
+    }
+    xmaxf = system_max(xmaxf, red, wps);
+    // diagonal-dominance margin (see the shared-memory refinement)
+    dmin = -system_max(-dmin, red, wps);
+    const double dmarg = dmin > 0.f ? static_cast<double>(dmin) * (1.0 - 1e-6) : 0.0;
+
+    int applied = 0;
+    for (int k = 0;; ++k) {
+        // neighbours of the first and last equation live in other threads
+        xfirst[tid] = xs[0];
+        xlast[tid] = xs[P - 1];
+        __syncthreads();
+        const double xl_nb = t > 0 ? xlast[tid - 1] : 0.0;
+        const double xr_nb = t < tps - 1 ? xfirst[tid + 1] : 0.0;
+        // residual r = d - A x in float64 from the stored float32 coefficients
+        float rmaxf = 0.f;
+#pragma unroll
+        for (int i = 0; i < P; ++i) {
+            const double xl = i > 0 ? xs[i > 0 ? i - 1 : 0] : xl_nb;
+            const double xr = i < P - 1 ? xs[i < P - 1 ? i + 1 : 0] : xr_nb;
+            double r;
+            if constexpr (COEF64) {
+                r = fma(-ca[i], xl, cd[i]);
+                r = fma(-cb[i], xs[i], r);
+                r = fma(-cc[i], xr, r);
+                const float4 q = ocoef[i];
+                la[i] = q.x;
+                lb[i] = q.y;
+                lc[i] = q.z;
+            } else {
+                r = fma(-static_cast<double>(oa[i]), xl, static_cast<double>(od[i]));
+                r = fma(-static_cast<double>(ob[i]), xs[i], r);
+                r = fma(-static_cast<double>(oc[i]), xr, r);
+                la[i] = oa[i];
+                lb[i] = ob[i];
+                lc[i] = oc[i];
+            }
+            const float rf = static_cast<float>(r);
+            rmaxf = fmaxf(rmaxf, fabsf(rf));
+            ld[i] = rf;
+        }
+        rmaxf = system_max(rmaxf, red, wps);
+        if (t == 0 && dmarg > 0.0 &&
+            static_cast<double>(rmaxf) * (1.0 + 1e-6) <= tol * static_cast<double>(xmaxf) * dmarg)
+            done_sys[s] = 1;
+        __syncthreads();
+        {
+            int all_done = 1;
+            for (int q = 0; q < spb; ++q) all_done &= done_sys[q];
+            __syncthreads();
+            if (all_done || k == max_iter) break;
+        }
+        int ex = 0;
+        if (rmaxf > 0.f) frexpf(rmaxf, &ex);
+        ex = ex < -120 ? -120 : (ex > 120 ? 120 : ex);
+        const float sigma = pow2_f32(-ex);
+#pragma unroll
+        for (int i = 0; i < P; ++i) ld[i] *= sigma;
+        cr_register_solve<P, PAD, SHUFFLE>(la, lb, lc, ld, log_m, log_tps, t, rows, bnd);
+        const bool was_done = done_sys[s] != 0 || rmaxf == 0.f;
+        const double inv_sigma = pow2_f64(ex);
+        float emaxf = 0.f;
+#pragma unroll
+        for (int i = 0; i < P; ++i) {
+            if (!was_done) xs[i] = fma(static_cast<double>(ld[i]), inv_sigma, xs[i]);
+            emaxf = fmaxf(emaxf, fabsf(ld[i]));
+        }
+        emaxf = system_max(emaxf, red, wps);
+        if (!was_done) ++applied;
+        if (t == 0 && (was_done || static_cast<double>(emaxf) * inv_sigma <= tol * static_cast<double>(xmaxf)))
+            done_sys[s] = 1;
+        __syncthreads();
+        int all_done = 1;
+        for (int q = 0; q < spb; ++q) all_done &= done_sys[q];
+        __syncthreads();
+        if (all_done) break;
+    }
+    if (valid) {
+#pragma unroll
+        for (int i = 0; i < P; i += 2) __stcs(reinterpret_cast<double2 *>(x + g + i), make_double2(xs[i], xs[i + 1]));
+        if (iters && t == 0) iters[sig0 + s] = applied;
+    }
+}
+
 namespace {
 
 // refined: layout bit 0 = float64 coefficient cache, bit 1 = compacted solver
 template <int PAD, int SHUFFLE>
 const void *tri_func_ps(bool refined, int layout, int io, int P) {
+    if (refined && layout >= 4) {
+        const bool c64 = layout == 5;
+        switch (P) {
+            case 2:
+                return c64 ? reinterpret_cast<const void *>(&tridiag_refined_reg_kernel<2, 1, PAD, SHUFFLE, 512>)
+                           : reinterpret_cast<const void *>(&tridiag_refined_reg_kernel<2, 0, PAD, SHUFFLE, 1024>);
+            case 4:
+                return c64 ? reinterpret_cast<const void *>(&tridiag_refined_reg_kernel<4, 1, PAD, SHUFFLE, 512>)
+                           : reinterpret_cast<const void *>(&tridiag_refined_reg_kernel<4, 0, PAD, SHUFFLE, 512>);
+            case 8:
+                return c64 ? reinterpret_cast<const void *>(&tridiag_refined_reg_kernel<8, 1, PAD, SHUFFLE, 256>)
+                           : reinterpret_cast<const void *>(&tridiag_refined_reg_kernel<8, 0, PAD, SHUFFLE, 256>);
+            case 16:
+                return c64 ? nullptr : reinterpret_cast<const void *>(&tridiag_refined_reg_kernel<16, 0, PAD, SHUFFLE, 256>);
+            default: return nullptr;
+        }
+    }
     if (refined) {
         switch (layout) {
             case 0: return reinterpret_cast<const void *>(&tridiag_refined_kernel<PAD, SHUFFLE, 0, 0>);
@@ -665,7 +877,7 @@ const void *tri_func_ps(bool refined, int layout, int io, int P) {
 }
 
 const void *tri_func(int pad, int shuffle, bool refined, int layout, int io, int P) {
-    if (pad < 0 || pad > 1 || shuffle < 0 || shuffle > 1 || layout < 0 || layout > 3 || io < 0 || io > 1)
+    if (pad < 0 || pad > 1 || shuffle < 0 || shuffle > 1 || layout < 0 || layout > 5 || io < 0 || io > 1)
         return nullptr;
     if (!refined && layout == 1 && (pad != 1 || io != 0)) return nullptr;
     if (!refined && layout == 2 && io != 0) return nullptr;
@@ -687,6 +899,13 @@ int tridiag_smem_bytes(int pad, int64_t n, int spb, bool refined, int layout, in
     }
     if (!refined && io == 1) return kTriTmaStages * 16 * spb * ni + spb * 16 * (pad ? tstride<1>(ni) : ni);
     if (!refined) return spb * 16 * (pad ? tstride<1>(ni) : ni);
+    if (layout >= 4) {  // register refinement: middle rows + boundary slots + neighbour x slots
+        const int tps = ni / P;
+        const int lp = ilog2(P);
+        const int threads = spb * tps;
+        return spb * 16 * (pad ? tstride<1>(tps) : tps) + threads * lp * 16 + threads * 16 +
+               (layout == 5 ? spb * ni * 16 : 0);
+    }
     int per = 0;
     switch (layout) {
         case 0: per = pad ? refined_sys_bytes<1, 0, 0>(ni, levels) : refined_sys_bytes<0, 0, 0>(ni, levels); break;

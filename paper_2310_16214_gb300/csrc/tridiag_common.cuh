@@ -148,36 +148,18 @@ __device__ __forceinline__ void cr_reduce(float &a, float &b, float &c, float &d
     d = nd;
 }
 
-// One system of the register-level CR (smem_layout 2), for the thread t of
-// the tps threads serving it.  ga..gd, x point at this thread's P equations;
-// rows is this system's padded middle system (tstride(tps) float4) and bnd
-// the block's boundary-equation slots ([thread][log2 P] float4).  Every
-// thread of the block calls it (two barriers plus those of the middle solve).
+// Register-level CR on the P equations a..d held by thread t of the tps
+// threads serving one system (the register form of smem_layout 2).  rows is
+// this system's padded middle system (tstride(tps) float4) and bnd the
+// block's boundary-equation slots ([thread][log2 P] float4).  On return d
+// holds x for the thread's equations (a, b, c are destroyed).  Every thread
+// of the block calls it: two barriers plus those of the middle solve.
 template <int P, int PAD, int SHUFFLE>
-__device__ __forceinline__ void cr_register_system(const float *ga, const float *gb, const float *gc,
-                                                   const float *gd, float *x, bool active, int log_m,
-                                                   int log_tps, int t, float4 *rows, float4 *bnd) {
+__device__ __forceinline__ void cr_register_solve(float (&a)[P], float (&b)[P], float (&c)[P], float (&d)[P],
+                                                  int log_m, int log_tps, int t, float4 *rows, float4 *bnd) {
     constexpr int LP = (P >= 16) ? 4 : (P >= 8) ? 3 : (P >= 4) ? 2 : 1;
     const int tps = 1 << log_tps;
     const int tid = threadIdx.x;
-    float a[P], b[P], c[P], d[P];
-    if (active) {
-        load_run<float, P>(ga, a);
-        load_run<float, P>(gb, b);
-        load_run<float, P>(gc, c);
-        load_run<float, P>(gd, d);
-    } else {
-#pragma unroll
-        for (int i = 0; i < P; ++i) {
-            a[i] = 0.f;
-            b[i] = 1.f;
-            c[i] = 0.f;
-            d[i] = 0.f;
-        }
-    }
-    if (t == 0) a[0] = 0.f;
-    if (t == tps - 1) c[P - 1] = 0.f;
-
     // phase A: every register level except local P-1; record the boundary
     // equations B_l = local 2^l - 1 as it stands after level l-1
     bnd[tid * LP + 0] = make_float4(a[0], b[0], c[0], d[0]);
@@ -221,6 +203,33 @@ __device__ __forceinline__ void cr_register_system(const float *ga, const float 
             d[i] = (d[i] - a[i] * xl - c[i] * d[i + dl]) * frcp(b[i]);
         }
     }
+}
+
+// One system of the register-level CR read from and written to global
+// memory: ga..gd, x point at this thread's P equations.
+template <int P, int PAD, int SHUFFLE>
+__device__ __forceinline__ void cr_register_system(const float *ga, const float *gb, const float *gc,
+                                                   const float *gd, float *x, bool active, int log_m,
+                                                   int log_tps, int t, float4 *rows, float4 *bnd) {
+    const int tps = 1 << log_tps;
+    float a[P], b[P], c[P], d[P];
+    if (active) {
+        load_run<float, P>(ga, a);
+        load_run<float, P>(gb, b);
+        load_run<float, P>(gc, c);
+        load_run<float, P>(gd, d);
+    } else {
+#pragma unroll
+        for (int i = 0; i < P; ++i) {
+            a[i] = 0.f;
+            b[i] = 1.f;
+            c[i] = 0.f;
+            d[i] = 0.f;
+        }
+    }
+    if (t == 0) a[0] = 0.f;
+    if (t == tps - 1) c[P - 1] = 0.f;
+    cr_register_solve<P, PAD, SHUFFLE>(a, b, c, d, log_m, log_tps, t, rows, bnd);
     if (active) store_run<float, P>(x, d);
 }
 

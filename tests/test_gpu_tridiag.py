@@ -93,7 +93,7 @@ def test_refined_every_plan(bp, n):
     for p in bp.enumerate_plans(bp.OP_TRIDIAG_REFINED, bp.F32, n):
         x, it = run_refined(bp, sysm, p)
         assert tri_rel_err(x, ref).max() <= 1e-12, p
-        assert np.all(it >= 1) and np.all(it <= 10)
+        assert np.all(it >= 1) and np.all(it <= 10)  # at least one correction: x0 is only float32-accurate
 
 
 def test_refined_full_config_sampled(bp):
