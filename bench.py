@@ -71,6 +71,60 @@ def read_peaks():
         return 6800.0, "fallback"
 
 
+# DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum) of
+# the kernel as it stands, from one ncu capture of the same row at half the
+# batch, doubled; keyed by row and plan.  A launch whose plan was not captured
+# reports null.
+NCU_TRAFFIC = {
+    # tridiag_refined_reg_kernel<16, 2, 0, 1, 256>: 134.30 MB read + 27.66 MB
+    # written per half-size launch (the rest of x is still in L2 at kernel end)
+    ("refined_1024", (("P", 16), ("L", 64), ("spb", 1), ("shuffle", 1), ("pattern", 0), ("smem_layout", 6),
+                      ("smem_pad", 0), ("io", 0), ("cr_switch", 32))): 2 * (134301696 + 27660288),
+}
+
+# FP64 issue rate of one SM: 2 double-precision fused multiply-adds per clock
+# (the GB300 FP64 pipe; 152 SMs x 2 x 2 flop x 2.07 GHz = 1.26 TFLOP/s).
+FP64_FMA_PER_SM_CLK = 2
+DEFAULT_SM_MHZ = 2070.0
+
+
+def plan_key(plan):
+    if plan is None:
+        return None
+    d = plan.as_dict()
+    return tuple((k, d[k]) for k in ("P", "L", "spb", "shuffle", "pattern", "smem_layout", "smem_pad", "io",
+                                     "cr_switch"))
+
+
+def dominant_roofline(dom, dom_ms, peak, peak_kind, refined_iters, clocks):
+    """Roofline of the step's longest launch.
+
+    The refined solve is bound by the FP64 pipe, not by HBM: its algorithmic
+    work is 3 FP64 fused multiply-adds (6 flop) per unknown for every residual
+    and one FP64 add per unknown for every correction, with one residual more
+    than corrections (the last residual proves convergence).  Every other row
+    moves its algorithmic bytes once and is reported against HBM bandwidth."""
+    traffic = NCU_TRAFFIC.get((dom["name"], plan_key(dom["plan"])))
+    gbs = dom["bytes"] / (dom_ms * 1e-3) / 1e9
+    if dom["op"] == "refined" and refined_iters is not None:
+        import torch
+        c = refined_iters["mean"]
+        flops = dom["elems"] * (6.0 * (c + 1.0) + c)
+        sms = torch.cuda.get_device_properties(0).multi_processor_count
+        mhz = clocks.get("sm_max_mhz") or DEFAULT_SM_MHZ
+        fp64_peak = sms * FP64_FMA_PER_SM_CLK * 2 * mhz * 1e6 / 1e12
+        achieved = flops / (dom_ms * 1e-3) / 1e12
+        return {"bound": "alu", "pipe": "fp64", "kernel": dom["name"], "achieved": round(achieved, 4),
+                "peak": round(fp64_peak, 4),
+                "peak_kind": "derived (%d SMs x %d FP64 FMA/clk x 2 flop x %.0f MHz)" % (sms, FP64_FMA_PER_SM_CLK, mhz),
+                "unit": "TFLOP/s", "frac": round(achieved / fp64_peak, 4), "traffic": traffic,
+                "algorithmic_flops": flops, "algorithmic_bytes": dom["bytes"], "launch_ms": round(dom_ms, 5),
+                "hbm": {"achieved": round(gbs, 1), "peak": peak, "peak_kind": peak_kind, "frac": round(gbs / peak, 4)}}
+    return {"bound": "hbm", "kernel": dom["name"], "achieved": round(gbs, 1), "peak": peak,
+            "peak_kind": peak_kind, "unit": "GB/s", "frac": round(gbs / peak, 4),
+            "traffic": traffic, "algorithmic_bytes": dom["bytes"], "launch_ms": round(dom_ms, 5)}
+
+
 class ClockSampler:
     """nvidia-smi clocks and throttle reasons sampled during the timed region."""
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
@@ -86,7 +140,7 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
-                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+                 "-lms", "50"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.thread = threading.Thread(target=self._read, daemon=True)
             self.thread.start()
         except Exception:
@@ -134,6 +188,24 @@ def dist_setup():
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     return world, rank, local
+
+
+def max_over_ranks(x: float, world: int, device) -> float:
+    """The largest value of x over all ranks (the slowest rank's time); the
+    only collective of the bench, outside the timed region."""
+    if world == 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(world: int, elems_per_rank: int, step_ms: float) -> float:
+    """Whole-job throughput in Gelem/s: every rank runs its own replica of the
+    per-GPU workload (weak scaling), all in the same max-over-ranks step time."""
+    return world * elems_per_rank / (step_ms * 1e-3) / 1e9
 
 
 # ----------------------------------------------------------------- workload
@@ -290,22 +362,28 @@ def run_ours(args):
     wl = Workload(torch, bp, dev, scale=args.scale, rows=args.rows.split(",") if args.rows else None,
                   plans=args.plans, plan_json=plan_json, seed=args.seed)
     stream = torch.cuda.current_stream()
-    ev = {it["name"]: [] for it in wl.items}
 
-    def step(record: bool):
+    def make_events(k):
+        return {it["name"]: [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                             for _ in range(k)] for it in wl.items}
+
+    def step(evs=None, idx=0):
         for it in wl.items:
-            if record:
-                e0 = torch.cuda.Event(enable_timing=True)
-                e1 = torch.cuda.Event(enable_timing=True)
-                e0.record(stream)
+            if evs is None:
                 it["fn"]()
-                e1.record(stream)
-                ev[it["name"]].append((e0, e1))
-            else:
-                it["fn"]()
+                continue
+            e0, e1 = evs[it["name"]][idx]
+            e0.record(stream)
+            it["fn"]()
+            e1.record(stream)
 
-    for _ in range(args.warmup):
-        step(False)
+    # every event of the timed region exists before it starts, and one
+    # warm-up step records events too, so no first-use cost lands in a timed
+    # launch
+    ev = make_events(args.steps)
+    step(make_events(1))
+    for _ in range(max(0, args.warmup - 1)):
+        step()
     torch.cuda.synchronize()
 
     def barrier():
@@ -319,24 +397,19 @@ def run_ours(args):
     sampler = ClockSampler(local if world > 1 else 0)
     sampler.start()
     for _ in range(2):
-        step(False)
+        step()
     barrier()
     t0 = torch.cuda.Event(enable_timing=True)
     t1 = torch.cuda.Event(enable_timing=True)
     torch.cuda.nvtx.range_push("timed")  # lets a profiler keep exactly the timed launches
     t0.record(stream)
-    for _ in range(args.steps):
-        step(True)
+    for k in range(args.steps):
+        step(ev, k)
     t1.record(stream)
     torch.cuda.nvtx.range_pop()
     barrier()
     clocks = sampler.stop()
-    total_ms = t0.elapsed_time(t1)
-    if world > 1:
-        import torch.distributed as dist
-        tt = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        total_ms = float(tt.item())
+    total_ms = max_over_ranks(t0.elapsed_time(t1), world, dev)
 
     per_item, per_item_median = {}, {}
     for it in wl.items:
@@ -355,15 +428,15 @@ def run_ours(args):
         d["gb_s"] = d["bytes"] / (d["ms"] * 1e-3) / 1e9
         d["hbm_frac"] = d["gb_s"] / peak
         d["ms"] = round(d["ms"], 4)
+    refined_iters = None
+    if hasattr(wl, "iters"):
+        it_np = wl.iters.cpu().numpy()
+        refined_iters = {"mean": round(float(it_np.mean()), 3), "max": int(it_np.max()), "min": int(it_np.min())}
     # dominant kernel: the launch with the largest share of the step
     dom = max(wl.items, key=lambda it: per_item[it["name"]])
-    dom_ms = per_item[dom["name"]]
-    achieved = dom["bytes"] / (dom_ms * 1e-3) / 1e9
-    roofline = {"bound": "hbm", "kernel": dom["name"], "achieved": round(achieved, 1), "peak": peak,
-                "peak_kind": peak_kind, "unit": "GB/s", "frac": round(achieved / peak, 4),
-                "traffic": None, "algorithmic_bytes": dom["bytes"], "launch_ms": round(dom_ms, 5)}
+    roofline = dominant_roofline(dom, per_item[dom["name"]], peak, peak_kind, refined_iters, clocks)
     step_ms = total_ms / args.steps
-    value = world * wl.elems / (step_ms * 1e-3) / 1e9
+    value = job_value(world, wl.elems, step_ms)
     launches_per_step = len(wl.items)
     items_out = {it["name"]: {"ms": round(per_item[it["name"]], 5),
                               "median_ms": round(per_item_median[it["name"]], 5),
@@ -372,10 +445,6 @@ def run_ours(args):
                                        if k in ("P", "L", "spb", "smem_layout", "smem_pad", "io", "cr_switch",
                                                 "shuffle", "pattern")}}
                  for it in wl.items}
-    refined_iters = None
-    if hasattr(wl, "iters"):
-        it_np = wl.iters.cpu().numpy()
-        refined_iters = {"mean": round(float(it_np.mean()), 3), "max": int(it_np.max()), "min": int(it_np.min())}
 
     e2e = measure_e2e(torch, wl, stream, args) if rank == 0 and not args.no_e2e else None
     cpu = cpu_baseline(args) if (rank == 0 and world == 1 and not args.no_cpu) else None
@@ -508,7 +577,12 @@ def run_reference(args):
     world, rank, local = dist_setup()
     if rank != 0:
         return
-    items = oracle_sample(max(1, args.cpu_rows // 16))
+    # size each step's sample so the whole run stays near 90 s of CPU time
+    cal_rows = 256
+    _, cal_secs = oracle_run(oracle_sample(cal_rows))
+    per_row = max(cal_secs / cal_rows, 1e-9)
+    rows = int(90.0 / max(1, args.steps + args.warmup) / per_row)
+    items = oracle_sample(max(1, min(args.cpu_rows // 16, rows)))
     for _ in range(args.warmup):
         oracle_run(items)
     elems = 0
@@ -634,7 +708,7 @@ def precision_report(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=300)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--scale", type=float, default=1.0, help="fraction of the full batch sizes (testing only)")

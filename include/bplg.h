@@ -91,7 +91,8 @@ typedef enum { BPLG_TC_BF16 = 0, BPLG_TC_F16 = 1 } bplg_tc_precision;
  *           also cached as float64, bit 1 one array per CR level; 4 every
  *           equation in registers (register-level CR), 5 the same with the
  *           coefficients held as float64 registers and their float32
- *           copies in shared memory (P <= 8).
+ *           copies in shared memory (P <= 8), 6 the same with the float32
+ *           coefficients in shared memory only (fewer registers per thread).
  *   smem_pad 1: pad shared-memory rows against bank conflicts.
  *   io      FFT: 0 registers <-> global memory directly, 1 staged through
  *           shared memory with 16-byte accesses, 2 persistent blocks fed by
@@ -202,7 +203,11 @@ int bplg_tridiag_batched(const float *a, const float *b, const float *c, const f
  * max|e| <= tol * max|x0|, or, before another solve, when its residual
  * bounds the error: for strictly diagonally dominant rows
  * max|r| / min_i(|b_i| - |a_i| - |c_i|) <= tol * max|x0|; and after at most
- * max_iter corrections.
+ * max_iter corrections.  The stopping tests are evaluated in float32 on
+ * the float32 maxima with a 1e-5 relative safety margin, against tol rounded
+ * toward zero; a test whose right-hand side falls below 2^-100 never stops a
+ * system (it then runs max_iter corrections).  The residual's float32 copy
+ * for the correction solve flushes magnitudes below 2^-126 to zero.
  *   x       device, float64 [batch][n] (must not alias the inputs).
  *   iters   device int32 [batch] (corrections applied per system) or NULL.
  *   n       power of two, 2 <= n <= 4096.

@@ -161,6 +161,32 @@ __global__ void __launch_bounds__(MAXT)
     }
 }
 
+// Size-specialised variant of fft_kernel (same plan, same arithmetic, same
+// shared-memory layout) for padded, directly loaded transforms of the large
+// sizes; its compile-time stage schedule (fft_fixed_stages) is described in
+// fft_common.cuh.
+template <int R, int LOGN, int DIR, int LAYOUT, int MAXT>
+__global__ void __launch_bounds__(MAXT)
+    fft_fixed_kernel(const float2 *in, float2 *out, const float2 *__restrict__ tw, int logn, int spb,
+                     int64_t batch) {
+    using S = FftShape<R, LOGN>;
+    (void)logn;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int tid = threadIdx.x;
+    const int s = tid >> S::LOGT;
+    const int j = tid & (S::T - 1);
+    const int64_t sig = static_cast<int64_t>(blockIdx.x) * spb + s;
+    const bool active = sig < batch;
+    const int sbase = s * sig_stride<LAYOUT, 1>(1 << LOGN);
+    float2 *buf2 = reinterpret_cast<float2 *>(smem_raw) + sbase;
+    float *buf1 = reinterpret_cast<float *>(smem_raw) + sbase;
+    const float2 *g = in + sig * (int64_t(1) << LOGN) + j;
+    float2 v[R];
+#pragma unroll
+    for (int m = 0; m < R; ++m) v[m] = active ? __ldcs(g + m * S::T) : make_float2(0.f, 0.f);
+    fft_fixed_stages<R, LOGN, DIR, LAYOUT, 0>(v, buf2, buf1, j, tw, out + sig * (int64_t(1) << LOGN), active);
+}
+
 // Persistent, TMA-pipelined variant (io = 2).  Grid = the resident-block
 // capacity of the device; each block walks tiles (spb consecutive signals)
 // tile = blockIdx.x, blockIdx.x + gridDim.x, ...  A ring of NS shared-memory
@@ -347,6 +373,84 @@ __global__ void __launch_bounds__(MAXT)
 
 constexpr int kFftTmaStages = 3;
 
+// The pipelined variant with the compile-time stage schedule: radix 16,
+// padded exchanges, n = 2^LOGN >= 512 (T >= 32, so the first stage reads the
+// ring slot directly and the last stage stores straight to global memory).
+// The ring, the bounded waits and the refill protocol are those of
+// fft_tma_kernel.
+template <int LOGN, int DIR, int MAXT, int NS>
+__global__ void __launch_bounds__(MAXT)
+    fft_tma_fixed_kernel(const float2 *in, float2 *out, const float2 *__restrict__ tw, int logn, int spb,
+                         int64_t batch, int64_t ntiles, int slot_elems) {
+    using S = FftShape<16, LOGN>;
+    static_assert(S::T >= 32, "the slot is read directly only with T >= 32");
+    constexpr int N = 1 << LOGN;
+    constexpr int STRIDE = N + N / 16;
+    (void)logn;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    __shared__ __align__(8) uint64_t full[NS];
+    const int tid = threadIdx.x;
+    const int s = tid >> S::LOGT;
+    const int j = tid & (S::T - 1);
+    float2 *slots = reinterpret_cast<float2 *>(smem_raw);
+    int issued[NS], consumed[NS];
+#pragma unroll
+    for (int q = 0; q < NS; ++q) issued[q] = consumed[q] = 0;
+
+    auto issue = [&](int64_t tile, int q) {
+        const int64_t sig0 = tile * spb;
+        const int64_t left = batch - sig0;
+        const int nv = left < spb ? static_cast<int>(left) : spb;
+        const uint32_t bytes = static_cast<uint32_t>(nv) * static_cast<uint32_t>(N) * 8u;
+        mbar_arrive_expect_tx(&full[q], bytes);
+        tma_load_1d(slots + static_cast<size_t>(q) * slot_elems, in + sig0 * N, bytes, &full[q]);
+        ++issued[q];
+    };
+
+    if (tid == 0) {
+#pragma unroll
+        for (int q = 0; q < NS; ++q) mbar_init(&full[q], 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    if (tid == 0) {
+#pragma unroll
+        for (int q = 0; q < NS; ++q) {
+            const int64_t tile = blockIdx.x + static_cast<int64_t>(q) * gridDim.x;
+            if (tile < ntiles) issue(tile, q);
+        }
+    }
+
+    int k = 0;
+    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++k) {
+        const int q = k % NS;
+        const uint32_t parity = static_cast<uint32_t>(k / NS) & 1u;
+        float2 *slot = slots + static_cast<size_t>(q) * slot_elems;
+        const int64_t sig0 = tile * spb;
+        const bool active = sig0 + s < batch;
+        const bool ok = __syncthreads_and(mbar_wait_bounded(&full[q], parity));
+        if (!ok) {
+            if (tid == 0) {  // drain this block's copies in flight, then leave
+#pragma unroll
+                for (int qq = 0; qq < NS; ++qq)
+                    if (issued[qq] > consumed[qq]) mbar_wait_bounded(&full[qq], static_cast<uint32_t>(consumed[qq]) & 1u);
+            }
+            return;
+        }
+        if (tid == 0) ++consumed[q];
+        float2 v[16];
+#pragma unroll
+        for (int m = 0; m < 16; ++m) v[m] = slot[s * N + j + m * S::T];
+        fft_fixed_stages<16, LOGN, DIR, 0, 0>(v, slot + s * STRIDE, nullptr, j, tw, out + (sig0 + s) * N, active);
+        __syncthreads();  // every read of the slot is done: refill it
+        const int64_t next = tile + static_cast<int64_t>(NS) * gridDim.x;
+        if (tid == 0 && next < ntiles) {
+            fence_proxy_async();
+            issue(next, q);
+        }
+    }
+}
+
 // Twiddle table: tw[M + k] = exp(-2 pi i k / M) for M = 2, 4, ..., 2^max_log,
 // computed in float64 and rounded once to float32.
 __global__ void twiddle_init_kernel(float2 *tw, int max_log) {
@@ -381,8 +485,39 @@ const void *fft_func_io_t(int io) {
     }
 }
 
+// Size-specialised kernels: radix 16, padded, direct io, n = 2^10 .. 2^14.
+template <int DIR, int LAYOUT, int MAXT>
+const void *fft_fixed_func(int logn) {
+    switch (logn) {
+        case 10: return reinterpret_cast<const void *>(&fft_fixed_kernel<16, 10, DIR, LAYOUT, MAXT>);
+        case 11: return reinterpret_cast<const void *>(&fft_fixed_kernel<16, 11, DIR, LAYOUT, MAXT>);
+        case 12: return reinterpret_cast<const void *>(&fft_fixed_kernel<16, 12, DIR, LAYOUT, MAXT>);
+        case 13: return reinterpret_cast<const void *>(&fft_fixed_kernel<16, 13, DIR, LAYOUT, MAXT>);
+        case 14: return reinterpret_cast<const void *>(&fft_fixed_kernel<16, 14, DIR, LAYOUT, MAXT>);
+        default: return nullptr;
+    }
+}
+
+template <int DIR, int MAXT>
+const void *fft_tma_fixed_func(int logn) {
+    switch (logn) {
+        case 10: return reinterpret_cast<const void *>(&fft_tma_fixed_kernel<10, DIR, MAXT, kFftTmaStages>);
+        case 11: return reinterpret_cast<const void *>(&fft_tma_fixed_kernel<11, DIR, MAXT, kFftTmaStages>);
+        case 12: return reinterpret_cast<const void *>(&fft_tma_fixed_kernel<12, DIR, MAXT, kFftTmaStages>);
+        case 13: return reinterpret_cast<const void *>(&fft_tma_fixed_kernel<13, DIR, MAXT, kFftTmaStages>);
+        case 14: return reinterpret_cast<const void *>(&fft_tma_fixed_kernel<14, DIR, MAXT, kFftTmaStages>);
+        default: return nullptr;
+    }
+}
+
 template <int R, int DIR, int LAYOUT, int PAD>
-const void *fft_func_io(int io, int threads) {
+const void *fft_func_io(int io, int threads, int logn) {
+    if constexpr (R == 16 && PAD == 1) {
+        if (io == 0 && logn >= 10 && logn <= 14)
+            return threads <= 512 ? fft_fixed_func<DIR, LAYOUT, 512>(logn) : fft_fixed_func<DIR, LAYOUT, 1024>(logn);
+        if (LAYOUT == 0 && io == 2 && logn >= 10 && logn <= 14)
+            return threads <= 512 ? fft_tma_fixed_func<DIR, 512>(logn) : fft_tma_fixed_func<DIR, 1024>(logn);
+    }
     if constexpr (R == 16) {
         if (threads <= 512) return fft_func_io_t<R, DIR, LAYOUT, PAD, 512>(io);
     }
@@ -390,26 +525,27 @@ const void *fft_func_io(int io, int threads) {
 }
 
 template <int R, int DIR>
-const void *fft_func_rd(int layout, int pad, int io, int threads) {
-    if (layout == 0) return pad ? fft_func_io<R, DIR, 0, 1>(io, threads) : fft_func_io<R, DIR, 0, 0>(io, threads);
-    return pad ? fft_func_io<R, DIR, 1, 1>(io, threads) : fft_func_io<R, DIR, 1, 0>(io, threads);
+const void *fft_func_rd(int layout, int pad, int io, int threads, int logn) {
+    if (layout == 0)
+        return pad ? fft_func_io<R, DIR, 0, 1>(io, threads, logn) : fft_func_io<R, DIR, 0, 0>(io, threads, logn);
+    return pad ? fft_func_io<R, DIR, 1, 1>(io, threads, logn) : fft_func_io<R, DIR, 1, 0>(io, threads, logn);
 }
 
 template <int DIR>
-const void *fft_func_d(int radix, int layout, int pad, int io, int threads) {
+const void *fft_func_d(int radix, int layout, int pad, int io, int threads, int logn) {
     switch (radix) {
-        case 2: return fft_func_rd<2, DIR>(layout, pad, io, threads);
-        case 4: return fft_func_rd<4, DIR>(layout, pad, io, threads);
-        case 8: return fft_func_rd<8, DIR>(layout, pad, io, threads);
-        case 16: return fft_func_rd<16, DIR>(layout, pad, io, threads);
+        case 2: return fft_func_rd<2, DIR>(layout, pad, io, threads, logn);
+        case 4: return fft_func_rd<4, DIR>(layout, pad, io, threads, logn);
+        case 8: return fft_func_rd<8, DIR>(layout, pad, io, threads, logn);
+        case 16: return fft_func_rd<16, DIR>(layout, pad, io, threads, logn);
         default: return nullptr;
     }
 }
 
-const void *fft_func(int radix, int dir, int layout, int pad, int io, int threads) {
+const void *fft_func(int radix, int dir, int layout, int pad, int io, int threads, int logn) {
     if (layout < 0 || layout > 1 || pad < 0 || pad > 1 || io < 0 || io > 2) return nullptr;
-    return dir < 0 ? fft_func_d<-1>(radix, layout, pad, io, threads)
-                   : fft_func_d<1>(radix, layout, pad, io, threads);
+    return dir < 0 ? fft_func_d<-1>(radix, layout, pad, io, threads, logn)
+                   : fft_func_d<1>(radix, layout, pad, io, threads, logn);
 }
 
 std::mutex g_tw_mu;
@@ -477,7 +613,7 @@ int twiddles_for_current_device(const void **tw) {
 bool fft_launch_info(const bplg_plan &p, int64_t n, int64_t batch, int dir, Launch *out) {
     std::string why;
     if (!plan_structurally_valid(p, BPLG_F32, n, &why)) return false;
-    const void *f = fft_func(p.radix, dir, p.smem_layout, p.smem_pad, p.io, p.L);
+    const void *f = fft_func(p.radix, dir, p.smem_layout, p.smem_pad, p.io, p.L, ilog2(n));
     if (!f) return false;
     out->func = f;
     out->threads = p.L;
@@ -627,7 +763,7 @@ extern "C" int bplg_fft_batched_noalloc(const void *in, void *out, int64_t n, in
     }
     if (p.op != BPLG_OP_FFT || !plan_structurally_valid(p, BPLG_F32, n, nullptr) || p.io > 1)
         return set_error(BPLG_ERR_INVALID_PLAN, "fft no-alloc: invalid plan (the pipelined io mode is not offered here)");
-    const void *func = fft_func(p.radix, dir, p.smem_layout, p.smem_pad, p.io, p.L);
+    const void *func = fft_func(p.radix, dir, p.smem_layout, p.smem_pad, p.io, p.L, ilog2(n));
     if (!func) return set_error(BPLG_ERR_INVALID_PLAN, "fft no-alloc: plan has no kernel");
     const int smem = fft_smem_bytes(p.radix, p.smem_layout, p.smem_pad, p.io, n, p.spb);
     cudaFuncAttributes fa;

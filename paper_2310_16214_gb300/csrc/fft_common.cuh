@@ -141,4 +141,105 @@ __host__ __device__ __forceinline__ int sig_stride(int n) {
     return n + (p > 0 ? p : 1);
 }
 
+// Compile-time stage schedule of a padded radix-R Stockham transform of
+// n = 2^LOGN points (used by the size-specialised batched kernel and the
+// uneven-batch kernel).  With n, the radix and every stage's stride Ns known
+// at compile time, the stage loop unrolls and each exchange address is one per-thread
+// padded base plus a compile-time offset.  With the padding group G (16
+// float2 or 32 floats) and every stride a power of two, a stage's positions
+// base + off never carry across a group boundary (base mod G + off mod G < G:
+// base mod G is k < Ns plus a multiple of min(Ns R, G), off mod G at most
+// G - Ns), so pad(base + off) = pad(base) + off + off / G with pad(e) =
+// e + e / G; the same holds for the reads j + m T.  The generic kernel
+// recomputes shifts and pads for every element, which made the large
+// transforms issue-bound.
+template <int R, int LOGN>
+struct FftShape {
+    static constexpr int LR = clog2(R);
+    static constexpr int LR0 = LOGN % LR;  // radix 2^LR0 first stage when non-zero
+    static constexpr int LQ = LR - LR0;
+    static constexpr int LOGT = LOGN - LR;
+    static constexpr int T = 1 << LOGT;
+    static constexpr int NST = (LR0 ? 1 : 0) + LOGN / LR;
+    static constexpr int log_ns(int st) { return st == 0 ? 0 : (LR0 ? LR0 + (st - 1) * LR : st * LR); }
+};
+
+template <int G>
+__device__ __forceinline__ int pad_g(int e) {
+    return e + e / G;
+}
+
+// Output positions of stage ST as (per-thread base, compile-time offset of
+// register m), written to the padded exchange buffer or to global memory.
+template <int R, int LOGN, int ST>
+struct StageOut {
+    using S = FftShape<R, LOGN>;
+    static constexpr bool kMixed = ST == 0 && S::LR0 != 0;
+    static constexpr int LNS = S::log_ns(ST);
+    __device__ __forceinline__ static int base(int j) {
+        if constexpr (kMixed) return j << S::LR0;
+        else return ((j >> LNS) << (LNS + S::LR)) + (j & ((1 << LNS) - 1));
+    }
+    static constexpr int off(int m) {
+        return kMixed ? (((m & ((1 << S::LQ) - 1)) * S::T) << S::LR0) + (m >> S::LQ) : (m << LNS);
+    }
+};
+
+template <int R, int LOGN, int DIR, int LAYOUT, int ST>
+__device__ __forceinline__ void fft_fixed_stages(float2 (&v)[R], float2 *buf2, float *buf1, int j,
+                                                 const float2 *__restrict__ tw, float2 *gout, bool active) {
+    using S = FftShape<R, LOGN>;
+    using O = StageOut<R, LOGN, ST>;
+    constexpr int G = LAYOUT == 0 ? 16 : 32;
+    if constexpr (O::kMixed) {
+        first_stage_mixed<R, (1 << S::LR0), DIR>(v);
+    } else {
+        constexpr int LNS = O::LNS;
+        if constexpr (LNS > 0) {
+            const int k = j & ((1 << LNS) - 1);
+            const float2 *twk = tw + ((1 << LNS) << S::LR);
+#pragma unroll
+            for (int r = 1; r < R; ++r) {
+                float2 w = __ldg(twk + r * k);
+                if (DIR > 0) w.y = -w.y;
+                v[r] = cmul(v[r], w);
+            }
+        }
+        dft_codelet<R, DIR>(v);
+    }
+    const int ob = O::base(j);
+    if constexpr (ST == S::NST - 1) {
+        if (active) {
+#pragma unroll
+            for (int r = 0; r < R; ++r) __stcs(gout + ob + O::off(r), v[r]);
+        }
+    } else {
+        const int pb = pad_g<G>(ob);
+        const int pj = pad_g<G>(j);
+        constexpr int TP = S::T + S::T / G;
+        if constexpr (LAYOUT == 0) {
+            __syncthreads();
+#pragma unroll
+            for (int r = 0; r < R; ++r) buf2[pb + O::off(r) + O::off(r) / G] = v[r];
+            __syncthreads();
+#pragma unroll
+            for (int m = 0; m < R; ++m) v[m] = buf2[pj + m * TP];
+        } else {
+            __syncthreads();
+#pragma unroll
+            for (int r = 0; r < R; ++r) buf1[pb + O::off(r) + O::off(r) / G] = v[r].x;
+            __syncthreads();
+#pragma unroll
+            for (int m = 0; m < R; ++m) v[m].x = buf1[pj + m * TP];
+            __syncthreads();
+#pragma unroll
+            for (int r = 0; r < R; ++r) buf1[pb + O::off(r) + O::off(r) / G] = v[r].y;
+            __syncthreads();
+#pragma unroll
+            for (int m = 0; m < R; ++m) v[m].y = buf1[pj + m * TP];
+        }
+        fft_fixed_stages<R, LOGN, DIR, LAYOUT, ST + 1>(v, buf2, buf1, j, tw, gout, active);
+    }
+}
+
 }  // namespace bplg

@@ -113,9 +113,9 @@ bool plan_structurally_valid(const bplg_plan &p, int dtype, int64_t n, std::stri
                 return fail(why, "tridiag: shuffle/pad out of range");
             if (p.shuffle && p.cr_switch > 32) return fail(why, "tridiag: shuffle PCR needs cr_switch <= 32");
             if (p.op == BPLG_OP_TRIDIAG_REFINED && tps < 32) return fail(why, "refined: at least 32 threads per system");
-            if (p.smem_layout < 0 || p.smem_layout > (p.op == BPLG_OP_TRIDIAG_REFINED ? 5 : 2))
+            if (p.smem_layout < 0 || p.smem_layout > (p.op == BPLG_OP_TRIDIAG_REFINED ? 6 : 2))
                 return fail(why, "tridiag: smem_layout out of range (0 strided rows, 1 compacted levels, 2 register "
-                                 "levels; refined: bit 0 float64 coefficients, bit 1 compacted levels)");
+                                 "levels; refined: bit 0 float64 coefficients, bit 1 compacted levels, 4-6 register levels)");
             if (p.op == BPLG_OP_TRIDIAG && p.smem_layout == 2 && (p.P < 2 || p.io != 0))
                 return fail(why, "tridiag: register levels need P >= 2 and the per-block kernel");
             if (p.op == BPLG_OP_TRIDIAG && p.smem_layout == 1 && (p.smem_pad != 1 || p.io != 0))
@@ -229,7 +229,7 @@ std::vector<bplg_plan> enumerate_structural(int op, int dtype, int64_t n) {
                 }
             } else {
                 const int64_t mmax = tps < n ? tps : n;
-                const int layouts = op == BPLG_OP_TRIDIAG_REFINED ? 6 : 3;
+                const int layouts = op == BPLG_OP_TRIDIAG_REFINED ? 7 : 3;
                 const int ios = op == BPLG_OP_TRIDIAG ? 2 : 1;
                 for (int io = ios - 1; io >= 0; --io) {
                     for (int lay = layouts - 1; lay >= 0; --lay) {

@@ -34,7 +34,10 @@
 // (Varah's bound), so max|r| / delta <= tol max|x| bounds ||x - x*||.  With smem_layout 1 the
 // coefficients are also cached as float64 in shared memory, so the residual
 // needs no conversions (the float64 pipe is the bottleneck of this kernel).
+#include <cmath>
+
 #include "device_util.cuh"
+#include "fp_convert.cuh"
 #include "internal.h"
 #include "tma.cuh"
 #include "tridiag_common.cuh"
@@ -492,6 +495,12 @@ __device__ __forceinline__ double pow2_f64(int e) {
 }
 __device__ __forceinline__ float pow2_f32(int e) { return __int_as_float((127 + e) << 23); }
 
+// The stopping tests run in float32 on float32 maxima: products of at most
+// three float32 roundings, covered by the 1e-5 margins at their call sites.
+// A right-hand side near the subnormal range would lose that accuracy, so
+// below 2^-100 it becomes 0 and the test never stops the refinement.
+__device__ __forceinline__ float stop_rhs(float v) { return v >= 7.8886091e-31f ? v : 0.f; }
+
 // Shared memory of one system in the refined kernel, in bytes (16-byte
 // multiple): the solver's working rows (strided rows, or compacted levels and
 // the original-order x), original float32 rows, optional float64
@@ -506,7 +515,7 @@ template <int PAD, int SHUFFLE, int COEF64, int SOLVER>
 __global__ void __launch_bounds__(1024)
     tridiag_refined_kernel(const float *a, const float *b, const float *c, const float *d, double *x,
                            int32_t *iters, int logn, int log_m, int log_tps, int spb, int64_t batch,
-                           int max_iter, double tol) {
+                           int max_iter, float tolf) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ float red[32];
     __shared__ int done_sys[32];
@@ -552,8 +561,8 @@ __global__ void __launch_bounds__(1024)
             o[i] = q;
             w[widx(i)] = q;
             if constexpr (COEF64) {
-                ab[i] = make_double2(static_cast<double>(q.x), static_cast<double>(q.y));
-                cd[i] = make_double2(static_cast<double>(q.z), static_cast<double>(q.w));
+                ab[i] = make_double2(fpc::widen_f32(q.x), fpc::widen_f32(q.y));
+                cd[i] = make_double2(fpc::widen_f32(q.z), fpc::widen_f32(q.w));
             }
         }
     } else {
@@ -575,7 +584,7 @@ __global__ void __launch_bounds__(1024)
     float xmaxf = 0.f;
     for (int i = t; i < n; i += tps) {
         const float v = xsol(i);
-        xs[i] = static_cast<double>(v);
+        xs[i] = fpc::widen_f32(v);
         xmaxf = fmaxf(xmaxf, fabsf(v));
     }
     xmaxf = system_max(xmaxf, red, wps);
@@ -588,11 +597,17 @@ __global__ void __launch_bounds__(1024)
         dmin = fminf(dmin, fabsf(q.y) - fabsf(q.x) - fabsf(q.z));
     }
     dmin = -system_max(-dmin, red, wps);
-    const double dmarg = dmin > 0.f ? static_cast<double>(dmin) * (1.0 - 1e-6) : 0.0;
+    const float dmarg = dmin > 0.f ? dmin * (1.0f - 1e-5f) : 0.f;
+    // right-hand sides of the stopping tests below: 0 (never stop) unless
+    // comfortably above the float32 subnormal range
+    const float varah_rhs = stop_rhs(tolf * xmaxf * dmarg);
+    const float corr_rhs = stop_rhs(tolf * xmaxf);
 
     int applied = 0;
     for (int k = 0;; ++k) {
-        // residual r = d - A x in float64 from the stored float32 coefficients
+        // residual r = d - A x in float64 from the stored float32 coefficients;
+        // widening and narrowing are integer operations, so the FP64 pipe
+        // carries only the three fused multiply-adds per equation
         float rmaxf = 0.f;
         for (int i = t; i < n; i += tps) {
             const float4 q = o[i];
@@ -605,19 +620,18 @@ __global__ void __launch_bounds__(1024)
                 r = fma(-p.y, xs[i], r);
                 r = fma(-u.x, xr, r);
             } else {
-                r = fma(-static_cast<double>(q.x), xl, static_cast<double>(q.w));
-                r = fma(-static_cast<double>(q.y), xs[i], r);
-                r = fma(-static_cast<double>(q.z), xr, r);
+                r = fma(-fpc::widen_f32(q.x), xl, fpc::widen_f32(q.w));
+                r = fma(-fpc::widen_f32(q.y), xs[i], r);
+                r = fma(-fpc::widen_f32(q.z), xr, r);
             }
-            const float rf = static_cast<float>(r);
+            const float rf = fpc::narrow_f64_ftz(r);
             rmaxf = fmaxf(rmaxf, fabsf(rf));
             w[widx(i)] = make_float4(q.x, q.y, q.z, rf);
         }
         rmaxf = system_max(rmaxf, red, wps);
         // the residual already bounds the error: stop before solving when
         // max|r| / delta <= tol max|x|
-        if (t == 0 && dmarg > 0.0 &&
-            static_cast<double>(rmaxf) * (1.0 + 1e-6) <= tol * static_cast<double>(xmaxf) * dmarg)
+        if (t == 0 && rmaxf * (1.0f + 1e-5f) <= varah_rhs)
             done_sys[s] = 1;
         __syncthreads();
         {
@@ -636,16 +650,15 @@ __global__ void __launch_bounds__(1024)
         __syncthreads();
         solve();
         const bool was_done = done_sys[s] != 0 || rmaxf == 0.f;
-        const double inv_sigma = pow2_f64(ex);
         float emaxf = 0.f;
         for (int i = t; i < n; i += tps) {
             const float ep = xsol(i);
-            if (!was_done) xs[i] = fma(static_cast<double>(ep), inv_sigma, xs[i]);
+            if (!was_done) xs[i] += fpc::widen_f32_pow2(ep, ex);
             emaxf = fmaxf(emaxf, fabsf(ep));
         }
         emaxf = system_max(emaxf, red, wps);
         if (!was_done) ++applied;
-        if (t == 0 && (was_done || static_cast<double>(emaxf) * inv_sigma <= tol * static_cast<double>(xmaxf)))
+        if (t == 0 && (was_done || emaxf * pow2_f32(ex) * (1.0f + 1e-5f) <= corr_rhs))
             done_sys[s] = 1;
         __syncthreads();
         int all_done = 1;
@@ -663,24 +676,26 @@ __global__ void __launch_bounds__(1024)
     }
 }
 
-// Register-resident refinement (refined smem_layout 4 and 5).  Each thread
-// keeps its P equations' x in float64 and its working copy in registers; the
-// float32 correction solves are the register-level CR (the middle system and
-// boundary equations in shared memory), and the residual's neighbours across
-// threads come from two float64 slots per thread.  Layout 4 keeps the
-// original coefficients as float32 registers and widens them in every
-// residual; layout 5 keeps them as float64 registers (no conversion in the
-// residual -- on this GPU conversions occupy the float64 pipe) and their
-// float32 copies in shared memory for resetting the working copy.  The
-// arithmetic is that of the shared-memory refinement.
-template <int P, int COEF64, int PAD, int SHUFFLE, int MAXT>
+// Register-resident refinement (refined smem_layout 4, 5 and 6).  Each
+// thread keeps its P equations' x in float64 and its working copy in
+// registers; the float32 correction solves are the register-level CR (the
+// middle system and boundary equations in shared memory), and the residual's
+// neighbours across threads come from two float64 slots per thread.  The
+// original coefficients, which every residual and every new working copy
+// read, are kept (CO = 0, layout 4) as float32 registers; (CO = 1, layout 5)
+// as float64 registers with float32 copies in shared memory; or (CO = 2,
+// layout 6) as float32 rows in shared memory only, which frees 4P registers
+// per thread for occupancy.  Shared-memory rows are stored [row][thread] so a
+// warp's float4 accesses are contiguous.  The arithmetic is that of the
+// shared-memory refinement.
+template <int P, int CO, int PAD, int SHUFFLE, int MAXT>
 __global__ void __launch_bounds__(MAXT)
     tridiag_refined_reg_kernel(const float *ga, const float *gb, const float *gc, const float *gd, double *x,
                                int32_t *iters, int logn, int log_m, int log_tps, int spb, int64_t batch,
-                               int max_iter, double tol) {
+                               int max_iter, float tolf) {
     constexpr int LP = (P >= 16) ? 4 : (P >= 8) ? 3 : (P >= 4) ? 2 : 1;
-    constexpr int PF = COEF64 ? 1 : P;  // float32 coefficient registers (layout 4)
-    constexpr int PD = COEF64 ? P : 1;  // float64 coefficient registers (layout 5)
+    constexpr int PF = CO == 0 ? P : 1;  // float32 coefficient registers (layout 4)
+    constexpr int PD = CO == 1 ? P : 1;  // float64 coefficient registers (layout 5)
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ float red[32];
     __shared__ int done_sys[32];
@@ -700,7 +715,8 @@ __global__ void __launch_bounds__(MAXT)
     double *xfirst = reinterpret_cast<double *>(reinterpret_cast<float4 *>(smem_raw) + spb * mstride +
                                                 blockDim.x * LP);
     double *xlast = xfirst + blockDim.x;
-    float4 *ocoef = reinterpret_cast<float4 *>(xlast + blockDim.x) + tid * P;  // layout 5: this thread's rows
+    // layouts 5 and 6: row i of this thread at ocoef[i * blockDim.x]
+    float4 *ocoef = reinterpret_cast<float4 *>(xlast + blockDim.x) + tid;
     const int64_t g = (sig0 + s) * n + static_cast<int64_t>(t) * P;
 
     float la[P], lb[P], lc[P], ld[P];
@@ -726,12 +742,14 @@ __global__ void __launch_bounds__(MAXT)
 #pragma unroll
     for (int i = 0; i < P; ++i) {
         dmin = fminf(dmin, fabsf(lb[i]) - fabsf(la[i]) - fabsf(lc[i]));
-        if constexpr (COEF64) {
-            ca[i] = static_cast<double>(la[i]);
-            cb[i] = static_cast<double>(lb[i]);
-            cc[i] = static_cast<double>(lc[i]);
-            cd[i] = static_cast<double>(ld[i]);
-            ocoef[i] = make_float4(la[i], lb[i], lc[i], ld[i]);
+        if constexpr (CO == 1) {
+            ca[i] = fpc::widen_f32(la[i]);
+            cb[i] = fpc::widen_f32(lb[i]);
+            cc[i] = fpc::widen_f32(lc[i]);
+            cd[i] = fpc::widen_f32(ld[i]);
+        }
+        if constexpr (CO != 0) {
+            ocoef[i * blockDim.x] = make_float4(la[i], lb[i], lc[i], ld[i]);
         } else {
             oa[i] = la[i];
             ob[i] = lb[i];
@@ -746,13 +764,17 @@ __global__ void __launch_bounds__(MAXT)
     float xmaxf = 0.f;
 #pragma unroll
     for (int i = 0; i < P; ++i) {
-        xs[i] = static_cast<double>(ld[i]);
+        xs[i] = fpc::widen_f32(ld[i]);
         xmaxf = fmaxf(xmaxf, fabsf(ld[i]));
     }
     xmaxf = system_max(xmaxf, red, wps);
     // diagonal-dominance margin (see the shared-memory refinement)
     dmin = -system_max(-dmin, red, wps);
-    const double dmarg = dmin > 0.f ? static_cast<double>(dmin) * (1.0 - 1e-6) : 0.0;
+    const float dmarg = dmin > 0.f ? dmin * (1.0f - 1e-5f) : 0.f;
+    // right-hand sides of the stopping tests below: 0 (never stop) unless
+    // comfortably above the float32 subnormal range
+    const float varah_rhs = stop_rhs(tolf * xmaxf * dmarg);
+    const float corr_rhs = stop_rhs(tolf * xmaxf);
 
     int applied = 0;
     for (int k = 0;; ++k) {
@@ -762,36 +784,45 @@ __global__ void __launch_bounds__(MAXT)
         __syncthreads();
         const double xl_nb = t > 0 ? xlast[tid - 1] : 0.0;
         const double xr_nb = t < tps - 1 ? xfirst[tid + 1] : 0.0;
-        // residual r = d - A x in float64 from the stored float32 coefficients
+        // residual r = d - A x in float64 from the stored float32 coefficients;
+        // widening and narrowing are integer operations, so the FP64 pipe
+        // carries only the three fused multiply-adds per equation
         float rmaxf = 0.f;
 #pragma unroll
         for (int i = 0; i < P; ++i) {
             const double xl = i > 0 ? xs[i > 0 ? i - 1 : 0] : xl_nb;
             const double xr = i < P - 1 ? xs[i < P - 1 ? i + 1 : 0] : xr_nb;
             double r;
-            if constexpr (COEF64) {
+            if constexpr (CO == 1) {
                 r = fma(-ca[i], xl, cd[i]);
                 r = fma(-cb[i], xs[i], r);
                 r = fma(-cc[i], xr, r);
-                const float4 q = ocoef[i];
+                const float4 q = ocoef[i * blockDim.x];
+                la[i] = q.x;
+                lb[i] = q.y;
+                lc[i] = q.z;
+            } else if constexpr (CO == 2) {
+                const float4 q = ocoef[i * blockDim.x];
+                r = fma(-fpc::widen_f32(q.x), xl, fpc::widen_f32(q.w));
+                r = fma(-fpc::widen_f32(q.y), xs[i], r);
+                r = fma(-fpc::widen_f32(q.z), xr, r);
                 la[i] = q.x;
                 lb[i] = q.y;
                 lc[i] = q.z;
             } else {
-                r = fma(-static_cast<double>(oa[i]), xl, static_cast<double>(od[i]));
-                r = fma(-static_cast<double>(ob[i]), xs[i], r);
-                r = fma(-static_cast<double>(oc[i]), xr, r);
+                r = fma(-fpc::widen_f32(oa[i]), xl, fpc::widen_f32(od[i]));
+                r = fma(-fpc::widen_f32(ob[i]), xs[i], r);
+                r = fma(-fpc::widen_f32(oc[i]), xr, r);
                 la[i] = oa[i];
                 lb[i] = ob[i];
                 lc[i] = oc[i];
             }
-            const float rf = static_cast<float>(r);
+            const float rf = fpc::narrow_f64_ftz(r);
             rmaxf = fmaxf(rmaxf, fabsf(rf));
             ld[i] = rf;
         }
         rmaxf = system_max(rmaxf, red, wps);
-        if (t == 0 && dmarg > 0.0 &&
-            static_cast<double>(rmaxf) * (1.0 + 1e-6) <= tol * static_cast<double>(xmaxf) * dmarg)
+        if (t == 0 && rmaxf * (1.0f + 1e-5f) <= varah_rhs)
             done_sys[s] = 1;
         __syncthreads();
         {
@@ -808,16 +839,15 @@ __global__ void __launch_bounds__(MAXT)
         for (int i = 0; i < P; ++i) ld[i] *= sigma;
         cr_register_solve<P, PAD, SHUFFLE>(la, lb, lc, ld, log_m, log_tps, t, rows, bnd);
         const bool was_done = done_sys[s] != 0 || rmaxf == 0.f;
-        const double inv_sigma = pow2_f64(ex);
         float emaxf = 0.f;
 #pragma unroll
         for (int i = 0; i < P; ++i) {
-            if (!was_done) xs[i] = fma(static_cast<double>(ld[i]), inv_sigma, xs[i]);
+            if (!was_done) xs[i] += fpc::widen_f32_pow2(ld[i], ex);
             emaxf = fmaxf(emaxf, fabsf(ld[i]));
         }
         emaxf = system_max(emaxf, red, wps);
         if (!was_done) ++applied;
-        if (t == 0 && (was_done || static_cast<double>(emaxf) * inv_sigma <= tol * static_cast<double>(xmaxf)))
+        if (t == 0 && (was_done || emaxf * pow2_f32(ex) * (1.0f + 1e-5f) <= corr_rhs))
             done_sys[s] = 1;
         __syncthreads();
         int all_done = 1;
@@ -838,19 +868,18 @@ namespace {
 template <int PAD, int SHUFFLE>
 const void *tri_func_ps(bool refined, int layout, int io, int P) {
     if (refined && layout >= 4) {
-        const bool c64 = layout == 5;
-        switch (P) {
-            case 2:
-                return c64 ? reinterpret_cast<const void *>(&tridiag_refined_reg_kernel<2, 1, PAD, SHUFFLE, 512>)
-                           : reinterpret_cast<const void *>(&tridiag_refined_reg_kernel<2, 0, PAD, SHUFFLE, 1024>);
-            case 4:
-                return c64 ? reinterpret_cast<const void *>(&tridiag_refined_reg_kernel<4, 1, PAD, SHUFFLE, 512>)
-                           : reinterpret_cast<const void *>(&tridiag_refined_reg_kernel<4, 0, PAD, SHUFFLE, 512>);
-            case 8:
-                return c64 ? reinterpret_cast<const void *>(&tridiag_refined_reg_kernel<8, 1, PAD, SHUFFLE, 256>)
-                           : reinterpret_cast<const void *>(&tridiag_refined_reg_kernel<8, 0, PAD, SHUFFLE, 256>);
-            case 16:
-                return c64 ? nullptr : reinterpret_cast<const void *>(&tridiag_refined_reg_kernel<16, 0, PAD, SHUFFLE, 256>);
+        switch (layout * 32 + P) {
+            case 4 * 32 + 2: return reinterpret_cast<const void *>(&tridiag_refined_reg_kernel<2, 0, PAD, SHUFFLE, 1024>);
+            case 4 * 32 + 4: return reinterpret_cast<const void *>(&tridiag_refined_reg_kernel<4, 0, PAD, SHUFFLE, 512>);
+            case 4 * 32 + 8: return reinterpret_cast<const void *>(&tridiag_refined_reg_kernel<8, 0, PAD, SHUFFLE, 256>);
+            case 4 * 32 + 16: return reinterpret_cast<const void *>(&tridiag_refined_reg_kernel<16, 0, PAD, SHUFFLE, 256>);
+            case 5 * 32 + 2: return reinterpret_cast<const void *>(&tridiag_refined_reg_kernel<2, 1, PAD, SHUFFLE, 512>);
+            case 5 * 32 + 4: return reinterpret_cast<const void *>(&tridiag_refined_reg_kernel<4, 1, PAD, SHUFFLE, 512>);
+            case 5 * 32 + 8: return reinterpret_cast<const void *>(&tridiag_refined_reg_kernel<8, 1, PAD, SHUFFLE, 256>);
+            case 6 * 32 + 2: return reinterpret_cast<const void *>(&tridiag_refined_reg_kernel<2, 2, PAD, SHUFFLE, 1024>);
+            case 6 * 32 + 4: return reinterpret_cast<const void *>(&tridiag_refined_reg_kernel<4, 2, PAD, SHUFFLE, 1024>);
+            case 6 * 32 + 8: return reinterpret_cast<const void *>(&tridiag_refined_reg_kernel<8, 2, PAD, SHUFFLE, 512>);
+            case 6 * 32 + 16: return reinterpret_cast<const void *>(&tridiag_refined_reg_kernel<16, 2, PAD, SHUFFLE, 256>);
             default: return nullptr;
         }
     }
@@ -877,7 +906,7 @@ const void *tri_func_ps(bool refined, int layout, int io, int P) {
 }
 
 const void *tri_func(int pad, int shuffle, bool refined, int layout, int io, int P) {
-    if (pad < 0 || pad > 1 || shuffle < 0 || shuffle > 1 || layout < 0 || layout > 5 || io < 0 || io > 1)
+    if (pad < 0 || pad > 1 || shuffle < 0 || shuffle > 1 || layout < 0 || layout > 6 || io < 0 || io > 1)
         return nullptr;
     if (!refined && layout == 1 && (pad != 1 || io != 0)) return nullptr;
     if (!refined && layout == 2 && io != 0) return nullptr;
@@ -899,12 +928,12 @@ int tridiag_smem_bytes(int pad, int64_t n, int spb, bool refined, int layout, in
     }
     if (!refined && io == 1) return kTriTmaStages * 16 * spb * ni + spb * 16 * (pad ? tstride<1>(ni) : ni);
     if (!refined) return spb * 16 * (pad ? tstride<1>(ni) : ni);
-    if (layout >= 4) {  // register refinement: middle rows + boundary slots + neighbour x slots
+    if (layout >= 4) {  // register refinement: middle rows + boundary slots + neighbour x slots (+ rows)
         const int tps = ni / P;
         const int lp = ilog2(P);
         const int threads = spb * tps;
         return spb * 16 * (pad ? tstride<1>(tps) : tps) + threads * lp * 16 + threads * 16 +
-               (layout == 5 ? spb * ni * 16 : 0);
+               (layout >= 5 ? spb * ni * 16 : 0);
     }
     int per = 0;
     switch (layout) {
@@ -958,6 +987,9 @@ int tridiag_launch(const bplg_plan &p, const float *a, const float *b, const flo
 int tridiag_refined_launch(const bplg_plan &p, const float *a, const float *b, const float *c,
                            const float *d, double *x, int64_t n, int64_t batch, int max_iter,
                            double tol, int32_t *iters, cudaStream_t s) {
+    // the kernels compare in float32 against a tolerance no larger than tol
+    float tolf = static_cast<float>(tol);
+    if (static_cast<double>(tolf) > tol) tolf = std::nextafter(tolf, 0.f);
     Launch li;
     if (!tridiag_launch_info(p, n, batch, true, &li))
         return set_error(BPLG_ERR_INVALID_PLAN, "tridiag refined: plan has no kernel");
@@ -965,7 +997,7 @@ int tridiag_refined_launch(const bplg_plan &p, const float *a, const float *b, c
     if (rc != BPLG_OK) return rc;
     int logn = ilog2(n), log_m = ilog2(p.cr_switch), log_tps = ilog2(n / p.P), spb = p.spb;
     void *args[] = {(void *)&a,    (void *)&b,  (void *)&c,     (void *)&d,  (void *)&x,      (void *)&iters, &logn,
-                    &log_m,        &log_tps,    &spb,           &batch,      &max_iter,       &tol};
+                    &log_m,        &log_tps,    &spb,           &batch,      &max_iter,       &tolf};
     cudaError_t e = cudaLaunchKernel(li.func, dim3(static_cast<unsigned>(li.blocks)), dim3(li.threads), args,
                                      static_cast<size_t>(li.smem), s);
     return e == cudaSuccess ? BPLG_OK : cuda_error(e, "tridiag refined launch");

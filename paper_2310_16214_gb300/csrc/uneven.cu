@@ -10,10 +10,12 @@
 // the batched kernels' (one signal per T threads), but every problem has its
 // own input and output pointers, so problems need not be contiguous.
 //   scan     256 threads; P = 4 for n <= 1024, else n / 256 (T <= 256)
-//   FFT      512 threads; radix 16 (mixed-radix first stage), T = n / 16
+//   FFT      512 threads; radix 16 (mixed-radix first stage), T = n / 16;
+//            n >= 1024 with the compile-time stage schedule
 //   tridiag  512 threads; P = 8 for n <= 4096, else 16; register CR levels,
 //            middle system of T equations by CR/PCR with shuffle PCR
 #include <algorithm>
+#include <cmath>
 #include <cstring>
 #include <memory>
 #include <vector>
@@ -189,6 +191,39 @@ __device__ __forceinline__ void fft_unit(const ItemDesc *items, const UnitDesc &
     }
 }
 
+// n >= 1024: the compile-time stage schedule of the size-specialised
+// batched kernel (constant exchange offsets, unrolled stages).  Not inlined:
+// each size keeps its own register allocation instead of all of them
+// merging into the kernel's.
+template <int LOGN, int DIR>
+__device__ __noinline__ void fft_unit_fixed(const ItemDesc *items, const UnitDesc &U,
+                                               const float2 *__restrict__ tw, float2 *buf) {
+    using S = FftShape<16, LOGN>;
+    const int tid = threadIdx.x;
+    const int s = tid >> S::LOGT;
+    const int j = tid & (S::T - 1);
+    const bool active = s < U.count;
+    float2 *b2 = buf + s * sig_stride<0, 1>(1 << LOGN);
+    const float2 *in = active ? static_cast<const float2 *>(items[U.first + s].in0) + j : nullptr;
+    float2 *out = active ? static_cast<float2 *>(items[U.first + s].out) : nullptr;
+    float2 v[16];
+#pragma unroll
+    for (int m = 0; m < 16; ++m) v[m] = active ? __ldcs(in + m * S::T) : make_float2(0.f, 0.f);
+    fft_fixed_stages<16, LOGN, DIR, 0, 0>(v, b2, nullptr, j, tw, out, active);
+}
+
+template <int DIR>
+__device__ __forceinline__ void fft_unit_any(const ItemDesc *items, const UnitDesc &U, const float2 *__restrict__ tw,
+                                             float2 *buf) {
+    switch (U.logn) {
+        case 10: fft_unit_fixed<10, DIR>(items, U, tw, buf); break;
+        case 11: fft_unit_fixed<11, DIR>(items, U, tw, buf); break;
+        case 12: fft_unit_fixed<12, DIR>(items, U, tw, buf); break;
+        case 13: fft_unit_fixed<13, DIR>(items, U, tw, buf); break;
+        default: fft_unit<DIR>(items, U, tw, buf); break;
+    }
+}
+
 __global__ void __launch_bounds__(kUnevenFftThreads)
     uneven_fft_kernel(const ItemDesc *items, const UnitDesc *units, int nunits, int *counter,
                       const float2 *__restrict__ tw) {
@@ -203,9 +238,9 @@ __global__ void __launch_bounds__(kUnevenFftThreads)
         if (u >= nunits) break;
         const UnitDesc U = units[u];
         if (U.flags < 0)
-            fft_unit<-1>(items, U, tw, buf);
+            fft_unit_any<-1>(items, U, tw, buf);
         else
-            fft_unit<1>(items, U, tw, buf);
+            fft_unit_any<1>(items, U, tw, buf);
         __syncthreads();  // the exchange buffer is reused by the next unit
     }
 }

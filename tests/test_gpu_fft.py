@@ -37,7 +37,7 @@ def run_fft(bp, z, direction, plan=None, in_place=False):
     return c64_from_dev(out)
 
 
-@pytest.mark.parametrize("n", [2, 4, 16, 32, 64, 128, 256, 1024, 2048, 4096, 16384])
+@pytest.mark.parametrize("n", [2, 4, 16, 32, 64, 128, 256, 1024, 2048, 4096, 8192, 16384])
 def test_every_plan_fwd_inv_ragged(bp, n):
     batch = 13 if n <= 4096 else 3
     z = si.fft_c64(batch, n, stream=n)
