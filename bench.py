@@ -411,11 +411,12 @@ def run_ours(args):
     clocks = sampler.stop()
     total_ms = max_over_ranks(t0.elapsed_time(t1), world, dev)
 
-    per_item, per_item_median = {}, {}
+    per_item, per_item_median, per_item_pct = {}, {}, {}
     for it in wl.items:
-        ms = [a.elapsed_time(b) for a, b in ev[it["name"]]]
+        ms = sorted(a.elapsed_time(b) for a, b in ev[it["name"]])
         per_item[it["name"]] = statistics.mean(ms)
         per_item_median[it["name"]] = statistics.median(ms)
+        per_item_pct[it["name"]] = (ms[int(0.1 * (len(ms) - 1))], ms[int(0.9 * (len(ms) - 1))])
     per_op = {}
     for it in wl.items:
         d = per_op.setdefault(it["op"], {"ms": 0.0, "elems": 0, "bytes": 0})
@@ -440,12 +441,23 @@ def run_ours(args):
     launches_per_step = len(wl.items)
     items_out = {it["name"]: {"ms": round(per_item[it["name"]], 5),
                               "median_ms": round(per_item_median[it["name"]], 5),
+                              "p10_ms": round(per_item_pct[it["name"]][0], 5),
+                              "p90_ms": round(per_item_pct[it["name"]][1], 5),
+                              "mrows_s": round(it["batch"] / (per_item[it["name"]] * 1e-3) / 1e6, 1),
+                              "gflops": (round(5 * it["n"] * math.log2(it["n"]) * it["batch"]
+                                               / (per_item[it["name"]] * 1e-3) / 1e9, 1) if it["op"] == "fft" else None),
                               "gb_s": round(it["bytes"] / (per_item[it["name"]] * 1e-3) / 1e9, 1),
                               "plan": {k: v for k, v in it["plan"].as_dict().items()
                                        if k in ("P", "L", "spb", "smem_layout", "smem_pad", "io", "cr_switch",
                                                 "shuffle", "pattern")}}
                  for it in wl.items}
 
+    ext = None
+    if rank == 0 and not args.no_ext and wl.items:
+        try:
+            ext = external_refs(torch, per_item, peak)
+        except Exception as exc:  # the references are context; their absence does not fail the bench
+            ext = {"unavailable": str(exc)[:200]}
     e2e = measure_e2e(torch, wl, stream, args) if rank == 0 and not args.no_e2e else None
     cpu = cpu_baseline(args) if (rank == 0 and world == 1 and not args.no_cpu) else None
 
@@ -462,12 +474,116 @@ def run_ours(args):
                        "parallelism": "replicas" if world > 1 else "single"},
             "roofline": roofline, "per_op": per_op, "per_launch": items_out,
             "gpu_launches": launches_per_step * args.steps, "clocks": clocks, "refined_corrections": refined_iters,
-            "e2e": e2e, "cpu_baseline": cpu,
+            "e2e": e2e, "cpu_baseline": cpu, "external": ext,
         }
         print(json.dumps(line))
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
+
+
+def external_refs(torch, per_item, peak, reps: int = 20):
+    """The vendor libraries on the same workloads and GPU, timed like the
+    rows of the step (CUDA events on the current stream, median of `reps`
+    launches after 3 warm-ups): cuFFT cufftPlanMany C2C for every FFT row,
+    CUB's segmented InclusiveSumByKey for every scan row (and, for n = 8192,
+    one InclusiveSum call per signal), cuSPARSE gtsv2StridedBatch for every
+    tridiagonal row.  Context only: none of it is on the library's path.
+    `ours_speedup` = the library's mean time / the reference's median time."""
+    import ctypes
+    lib = ctypes.CDLL(os.path.join(ROOT, "paper_2310_16214_gb300", "_lib", "libbplg_extref.so"))
+    vp, i64, szp = ctypes.c_void_p, ctypes.c_int64, ctypes.POINTER(ctypes.c_size_t)
+    lib.extref_scan_bykey.argtypes = [ctypes.c_int, vp, vp, i64, i64, vp, szp, vp]
+    lib.extref_scan_each.argtypes = [ctypes.c_int, vp, vp, i64, i64, vp, szp, vp]
+    lib.extref_fft_c2c.argtypes = [vp, vp, i64, i64, ctypes.c_int, vp]
+    lib.extref_gtsv2.argtypes = [vp, vp, vp, vp, i64, i64, vp, szp, vp]
+    st = torch.cuda.current_stream()
+    sh = vp(st.cuda_stream)
+    dev = torch.device("cuda", torch.cuda.current_device())
+
+    def ok(rc, what):
+        if rc != 0:
+            raise RuntimeError("%s failed (%d)" % (what, rc))
+
+    def timeit(fn, pre=None):
+        for _ in range(3):
+            if pre:
+                pre()
+            fn()
+        evs = []
+        for _ in range(reps):
+            if pre:
+                pre()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(st)
+            fn()
+            e1.record(st)
+            evs.append((e0, e1))
+        torch.cuda.synchronize()
+        return statistics.median(a.elapsed_time(b) for a, b in evs)
+
+    def entry(name, ms, elems, nbytes, rows):
+        e = {"ms": round(ms, 5), "gelem_s": round(elems / (ms * 1e-3) / 1e9, 2),
+             "hbm_frac": round(nbytes / (ms * 1e-3) / 1e9 / peak, 4)}
+        if name in per_item:
+            e["ours_speedup"] = round(ms / per_item[name], 3)
+        rows[name] = e
+
+    out = {"cufft": {}, "cub_scan": {}, "cusparse_gtsv2": {}}
+    for n in FFT_SIZES:
+        batch = FFT_TOTAL // n
+        zin = torch.rand(2 * n * batch, device=dev) * 2 - 1
+        zout = torch.empty_like(zin)
+        for d, tag in ((-1, "fwd"), (1, "inv")):
+            ms = timeit(lambda d=d: ok(lib.extref_fft_c2c(vp(zin.data_ptr()), vp(zout.data_ptr()), n, batch, d, sh),
+                                       "cufft"))
+            entry("fft_%s_%d" % (tag, n), ms, n * batch, 16 * n * batch, out["cufft"])
+        del zin, zout
+    for dname, dt, tdt in (("i32", 0, torch.int32), ("f32", 1, torch.float32)):
+        for n in SCAN_SIZES:
+            batch = SCAN_TOTAL // n
+            xin = (torch.randint(-1000, 1001, (n * batch,), device=dev, dtype=torch.int32).to(tdt))
+            xout = torch.empty_like(xin)
+            need = ctypes.c_size_t(0)
+            ok(lib.extref_scan_bykey(dt, vp(xin.data_ptr()), vp(xout.data_ptr()), n, batch, None, ctypes.byref(need),
+                                     sh), "cub bykey size")
+            tmp = torch.empty(max(1, need.value), dtype=torch.uint8, device=dev)
+            ms = timeit(lambda: ok(lib.extref_scan_bykey(dt, vp(xin.data_ptr()), vp(xout.data_ptr()), n, batch,
+                                                         vp(tmp.data_ptr()), ctypes.byref(need), sh), "cub bykey"))
+            entry("scan_%s_%d" % (dname, n), ms, n * batch, 8 * n * batch, out["cub_scan"])
+            if n == SCAN_SIZES[-1] and dname == "i32":
+                each = ctypes.c_size_t(0)
+                ok(lib.extref_scan_each(dt, vp(xin.data_ptr()), vp(xout.data_ptr()), n, batch, None,
+                                        ctypes.byref(each), sh), "cub each size")
+                tmp2 = torch.empty(max(1, each.value), dtype=torch.uint8, device=dev)
+                ms = timeit(lambda: ok(lib.extref_scan_each(dt, vp(xin.data_ptr()), vp(xout.data_ptr()), n, batch,
+                                                            vp(tmp2.data_ptr()), ctypes.byref(each), sh), "cub each"))
+                e = {"ms": round(ms, 5), "gelem_s": round(n * batch / (ms * 1e-3) / 1e9, 2),
+                     "calls": batch}
+                if "scan_i32_%d" % n in per_item:
+                    e["ours_speedup"] = round(ms / per_item["scan_i32_%d" % n], 3)
+                out["cub_scan"]["scan_i32_%d_one_call_per_signal" % n] = e
+            del xin, xout, tmp
+    for n in TRI_SIZES:
+        batch = TRI_TOTAL // n
+        a = torch.rand(batch, n, device=dev) * 2 - 1
+        c = torch.rand(batch, n, device=dev) * 2 - 1
+        a[:, 0] = 0
+        c[:, -1] = 0
+        b = a.abs() + c.abs() + 1 + torch.rand(batch, n, device=dev)
+        d = torch.rand(batch, n, device=dev) * 2 - 1
+        x = torch.empty_like(d)
+        need = ctypes.c_size_t(0)
+        ok(lib.extref_gtsv2(vp(a.data_ptr()), vp(b.data_ptr()), vp(c.data_ptr()), vp(x.data_ptr()), n, batch, None,
+                            ctypes.byref(need), sh), "gtsv2 size")
+        buf = torch.empty(max(1, need.value), dtype=torch.uint8, device=dev)
+        ms = timeit(lambda: ok(lib.extref_gtsv2(vp(a.data_ptr()), vp(b.data_ptr()), vp(c.data_ptr()),
+                                                vp(x.data_ptr()), n, batch, vp(buf.data_ptr()), ctypes.byref(need),
+                                                sh), "gtsv2"),
+                    pre=lambda: x.copy_(d))
+        entry("tridiag_%d" % n, ms, n * batch, 20 * n * batch, out["cusparse_gtsv2"])
+        del a, b, c, d, x, buf
+    return out
 
 
 def measure_e2e(torch, wl, stream, args):
@@ -565,12 +681,45 @@ def oracle_run(items):
     return elems, time.perf_counter() - t0
 
 
+def host_cores() -> int:
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count() or 1
+
+
+def oracle_run_parallel(items, cores: int):
+    """The same oracle calls with every item's rows split into `cores`
+    contiguous slices run by a thread pool (the oracle is C called through
+    ctypes, which releases the interpreter lock during the call)."""
+    from concurrent.futures import ThreadPoolExecutor
+    chunks = []
+    for kind, arg, x in items:
+        rows = (x[0] if kind == "thomas" else x).shape[0]
+        for c in range(cores):
+            lo, hi = rows * c // cores, rows * (c + 1) // cores
+            if hi > lo:
+                chunks.append((kind, arg, tuple(a[lo:hi] for a in x) if kind == "thomas" else x[lo:hi]))
+    with ThreadPoolExecutor(max_workers=cores) as ex:
+        t0 = time.perf_counter()
+        elems = sum(ex.map(lambda it: oracle_run([it])[0], chunks))
+        secs = time.perf_counter() - t0
+    return elems, secs
+
+
 def cpu_baseline(args):
+    """The oracle timed on the host: every core with the batch split across
+    threads (the headline figure, `cores` = threads used), and one thread."""
+    cores = host_cores()
     items = oracle_sample(args.cpu_rows)
-    elems, secs = oracle_run(items)
-    return {"value": round(elems / secs / 1e9, 6), "unit": "Gelem/s", "cores": 1, "kind": "oracle",
+    elems1, secs1 = oracle_run(items)
+    itemsp = oracle_sample(2 * args.cpu_rows)
+    elemsp, secsp = oracle_run_parallel(itemsp, cores)
+    return {"value": round(elemsp / secsp / 1e9, 6), "unit": "Gelem/s", "cores": cores, "kind": "oracle",
+            "single_thread": {"value": round(elems1 / secs1 / 1e9, 6), "cores": 1, "seconds": round(secs1, 2)},
             "sample": "%d elements across every row of the step (%d x 64 elements per FFT and tridiag size, "
-                      "x 256 per scan size), single-threaded C oracle, %.1f s" % (elems, args.cpu_rows, secs)}
+                      "x 256 per scan size) split over %d threads, %.1f s; the single-thread figure uses half "
+                      "that sample" % (elemsp, 2 * args.cpu_rows, cores, secsp)}
 
 
 def run_reference(args):
@@ -578,17 +727,18 @@ def run_reference(args):
     if rank != 0:
         return
     # size each step's sample so the whole run stays near 90 s of CPU time
+    cores = host_cores()
     cal_rows = 256
-    _, cal_secs = oracle_run(oracle_sample(cal_rows))
+    _, cal_secs = oracle_run_parallel(oracle_sample(cal_rows), cores)
     per_row = max(cal_secs / cal_rows, 1e-9)
     rows = int(90.0 / max(1, args.steps + args.warmup) / per_row)
     items = oracle_sample(max(1, min(args.cpu_rows // 16, rows)))
     for _ in range(args.warmup):
-        oracle_run(items)
+        oracle_run_parallel(items, cores)
     elems = 0
     secs = 0.0
     for _ in range(args.steps):
-        e, s = oracle_run(items)
+        e, s = oracle_run_parallel(items, cores)
         elems += e
         secs += s
     value = elems / secs / 1e9
@@ -598,8 +748,9 @@ def run_reference(args):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64 (oracle)",
         "data": "synthetic (seeded SplitMix64, paper-shaped batches)",
         "config": {"workload": WORKLOAD, "sample": "bounded per-step sample of every row"},
-        "cpu_baseline": {"value": round(value, 6), "unit": "Gelem/s", "kind": "oracle", "cores": 1,
-                         "sample": "%d elements per step" % (elems // max(1, args.steps))},
+        "cpu_baseline": {"value": round(value, 6), "unit": "Gelem/s", "kind": "oracle", "cores": cores,
+                         "sample": "%d elements per step, every row of the step, batch split over %d threads"
+                                   % (elems // max(1, args.steps), cores)},
         "e2e": {"value": round(value, 6), "unit": "Gelem/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line))
@@ -715,6 +866,7 @@ def main():
     ap.add_argument("--cpu-rows", type=int, default=131072)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-ext", action="store_true", help="skip the cuFFT / CUB / cuSPARSE references")
     ap.add_argument("--tune-report", action="store_true", help="tuned vs exhaustive Phi report instead of the bench")
     ap.add_argument("--precision-report", action="store_true",
                     help="tensor-core (BF16/FP16 split) vs float32 FFT: error and time per N")

@@ -3,6 +3,8 @@
 Every translation unit under csrc/ is compiled in parallel with
 ``-gencode arch=compute_103a,code=sm_103a`` and linked into
 ``paper_2310_16214_gb300/_lib/libbplg.so`` (CUDA runtime linked statically).
+The benchmark's external references (extref/extref.cu: CUB, cuFFT, cuSPARSE)
+go into a separate ``_lib/libbplg_extref.so`` that the library never loads.
 """
 from __future__ import annotations
 
@@ -20,6 +22,8 @@ INCLUDE = os.path.join(ROOT, "include")
 OUT_DIR = os.path.join(HERE, "_lib")
 OBJ_DIR = os.path.join(OUT_DIR, "obj")
 LIB = os.path.join(OUT_DIR, "libbplg.so")
+EXTREF_SRC = os.path.join(HERE, "extref", "extref.cu")
+EXTREF_LIB = os.path.join(OUT_DIR, "libbplg_extref.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
@@ -65,12 +69,28 @@ def _compile(src: str, verbose_ptxas: bool) -> str:
     return obj
 
 
+def _build_extref() -> str:
+    if _stale(EXTREF_LIB, [EXTREF_SRC]):
+        cuda_inc = os.path.join(os.path.dirname(os.path.dirname(nvcc())), "include")
+        tmp = EXTREF_LIB + ".tmp.%d" % os.getpid()
+        cmd = [nvcc()] + ARCH + ["-O3", "-std=c++17", "-Xcompiler", "-fPIC", "-shared",
+                                 "-I" + os.path.join(cuda_inc, "cccl"), EXTREF_SRC, "-o", tmp,
+                                 "-lcufft", "-lcusparse"]
+        r = subprocess.run(cmd, capture_output=True, text=True)
+        if r.returncode != 0:
+            raise RuntimeError("extref build failed:\n" + r.stderr[-8000:])
+        os.replace(tmp, EXTREF_LIB)
+    return EXTREF_LIB
+
+
 def build(verbose_ptxas: bool = False, jobs: int = 0) -> str:
     os.makedirs(OBJ_DIR, exist_ok=True)
     srcs = sources()
     jobs = jobs or min(len(srcs), os.cpu_count() or 4)
-    with cf.ThreadPoolExecutor(max_workers=jobs) as ex:
+    with cf.ThreadPoolExecutor(max_workers=jobs + 1) as ex:
+        ext = ex.submit(_build_extref)
         objs = list(ex.map(lambda s: _compile(s, verbose_ptxas), srcs))
+        ext.result()
     if _stale(LIB, objs):
         tmp = LIB + ".tmp.%d" % os.getpid()
         cmd = [nvcc()] + ARCH + ["-shared", "-Xcompiler", "-fPIC", "-o", tmp] + objs

@@ -451,6 +451,95 @@ __global__ void __launch_bounds__(MAXT)
     }
 }
 
+// Split-exchange pipelined variant (io 2 with smem_layout 1): radix 16,
+// n = 2^LOGN >= 1024.  The ring slots hold the tiles unpadded; the stage
+// exchanges go through a separate real/imaginary float buffer (the
+// multiplexed layout), so a slot is free as soon as the first stage has read
+// it and its refill starts right away, overlapping the rest of the tile's
+// stages.  This is what lets a transform that needs a whole SM per signal
+// (n = 16384: 1024 threads, one block per SM) keep a load in flight.
+template <int LOGN>
+struct SplitRing {
+    // slots that fit beside the exchange buffer of one signal in 227 KB
+    static constexpr int kSlotBytes = (1 << LOGN) * 8;
+    static constexpr int kExchBytes = ((1 << LOGN) + (1 << LOGN) / 32) * 4;
+    static constexpr int NS = (2 * kSlotBytes + kExchBytes <= 227 * 1024) ? 2 : 1;
+};
+
+template <int LOGN, int DIR, int MAXT>
+__global__ void __launch_bounds__(MAXT)
+    fft_tma_split_kernel(const float2 *in, float2 *out, const float2 *__restrict__ tw, int logn, int spb,
+                         int64_t batch, int64_t ntiles, int slot_elems) {
+    using S = FftShape<16, LOGN>;
+    constexpr int NS = SplitRing<LOGN>::NS;
+    constexpr int N = 1 << LOGN;
+    constexpr int STRIDE1 = N + N / 32;  // floats per signal in the exchange buffer
+    (void)logn;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    __shared__ __align__(8) uint64_t full[NS];
+    const int tid = threadIdx.x;
+    const int s = tid >> S::LOGT;
+    const int j = tid & (S::T - 1);
+    float2 *slots = reinterpret_cast<float2 *>(smem_raw);
+    float *xbuf = reinterpret_cast<float *>(slots + static_cast<size_t>(NS) * slot_elems) + s * STRIDE1;
+    int issued[NS], consumed[NS];
+#pragma unroll
+    for (int q = 0; q < NS; ++q) issued[q] = consumed[q] = 0;
+
+    auto issue = [&](int64_t tile, int q) {
+        const int64_t sig0 = tile * spb;
+        const int64_t left = batch - sig0;
+        const int nv = left < spb ? static_cast<int>(left) : spb;
+        const uint32_t bytes = static_cast<uint32_t>(nv) * static_cast<uint32_t>(N) * 8u;
+        mbar_arrive_expect_tx(&full[q], bytes);
+        tma_load_1d(slots + static_cast<size_t>(q) * slot_elems, in + sig0 * N, bytes, &full[q]);
+        ++issued[q];
+    };
+
+    if (tid == 0) {
+#pragma unroll
+        for (int q = 0; q < NS; ++q) mbar_init(&full[q], 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    if (tid == 0) {
+#pragma unroll
+        for (int q = 0; q < NS; ++q) {
+            const int64_t tile = blockIdx.x + static_cast<int64_t>(q) * gridDim.x;
+            if (tile < ntiles) issue(tile, q);
+        }
+    }
+
+    int k = 0;
+    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++k) {
+        const int q = k % NS;
+        const uint32_t parity = static_cast<uint32_t>(k / NS) & 1u;
+        const float2 *slot = slots + static_cast<size_t>(q) * slot_elems;
+        const int64_t sig0 = tile * spb;
+        const bool active = sig0 + s < batch;
+        const bool ok = __syncthreads_and(mbar_wait_bounded(&full[q], parity));
+        if (!ok) {
+            if (tid == 0) {  // drain this block's copies in flight, then leave
+#pragma unroll
+                for (int qq = 0; qq < NS; ++qq)
+                    if (issued[qq] > consumed[qq]) mbar_wait_bounded(&full[qq], static_cast<uint32_t>(consumed[qq]) & 1u);
+            }
+            return;
+        }
+        if (tid == 0) ++consumed[q];
+        float2 v[16];
+#pragma unroll
+        for (int m = 0; m < 16; ++m) v[m] = slot[s * N + j + m * S::T];
+        __syncthreads();  // every read of the slot is done: refill it now
+        const int64_t next = tile + static_cast<int64_t>(NS) * gridDim.x;
+        if (tid == 0 && next < ntiles) {
+            fence_proxy_async();
+            issue(next, q);
+        }
+        fft_fixed_stages<16, LOGN, DIR, 1, 0>(v, nullptr, xbuf, j, tw, out + (sig0 + s) * N, active);
+    }
+}
+
 // Twiddle table: tw[M + k] = exp(-2 pi i k / M) for M = 2, 4, ..., 2^max_log,
 // computed in float64 and rounded once to float32.
 __global__ void twiddle_init_kernel(float2 *tw, int max_log) {
@@ -510,6 +599,18 @@ const void *fft_tma_fixed_func(int logn) {
     }
 }
 
+template <int DIR, int MAXT>
+const void *fft_tma_split_func(int logn) {
+    switch (logn) {
+        case 10: return reinterpret_cast<const void *>(&fft_tma_split_kernel<10, DIR, MAXT>);
+        case 11: return reinterpret_cast<const void *>(&fft_tma_split_kernel<11, DIR, MAXT>);
+        case 12: return reinterpret_cast<const void *>(&fft_tma_split_kernel<12, DIR, MAXT>);
+        case 13: return reinterpret_cast<const void *>(&fft_tma_split_kernel<13, DIR, MAXT>);
+        case 14: return reinterpret_cast<const void *>(&fft_tma_split_kernel<14, DIR, MAXT>);
+        default: return nullptr;
+    }
+}
+
 template <int R, int DIR, int LAYOUT, int PAD>
 const void *fft_func_io(int io, int threads, int logn) {
     if constexpr (R == 16 && PAD == 1) {
@@ -517,6 +618,8 @@ const void *fft_func_io(int io, int threads, int logn) {
             return threads <= 512 ? fft_fixed_func<DIR, LAYOUT, 512>(logn) : fft_fixed_func<DIR, LAYOUT, 1024>(logn);
         if (LAYOUT == 0 && io == 2 && logn >= 10 && logn <= 14)
             return threads <= 512 ? fft_tma_fixed_func<DIR, 512>(logn) : fft_tma_fixed_func<DIR, 1024>(logn);
+        if (LAYOUT == 1 && io == 2 && logn >= 10 && logn <= 14)
+            return threads <= 512 ? fft_tma_split_func<DIR, 512>(logn) : fft_tma_split_func<DIR, 1024>(logn);
     }
     if constexpr (R == 16) {
         if (threads <= 512) return fft_func_io_t<R, DIR, LAYOUT, PAD, 512>(io);
@@ -554,6 +657,24 @@ std::unordered_map<int, float2 *> g_tw;
 }  // namespace
 
 // elements of one ring slot of the pipelined kernel (128-byte multiple)
+int fft_tma_slot_elems(int pad, int64_t n, int spb);
+
+// slots of the split-exchange ring: the tile unpadded
+static int split_slots(int64_t n) {
+    switch (ilog2(n)) {
+        case 10: return SplitRing<10>::NS;
+        case 11: return SplitRing<11>::NS;
+        case 12: return SplitRing<12>::NS;
+        case 13: return SplitRing<13>::NS;
+        default: return SplitRing<14>::NS;
+    }
+}
+
+int fft_tma_slot_elems_layout(int layout, int pad, int64_t n, int spb) {
+    if (layout == 1) return static_cast<int>((static_cast<int64_t>(spb) * n + 15) & ~int64_t(15));
+    return fft_tma_slot_elems(pad, n, spb);
+}
+
 int fft_tma_slot_elems(int pad, int64_t n, int spb) {
     const int logn = ilog2(n);
     (void)logn;
@@ -563,6 +684,10 @@ int fft_tma_slot_elems(int pad, int64_t n, int spb) {
 
 int fft_smem_bytes(int radix, int layout, int pad, int io, int64_t n, int spb) {
     const int logn = ilog2(n);
+    if (io == 2 && layout == 1) {  // split-exchange ring: slots + real/imaginary exchange buffer
+        const int64_t slot = fft_tma_slot_elems_layout(1, pad, n, spb);
+        return static_cast<int>(split_slots(n) * slot * 8 + static_cast<int64_t>(spb) * sig_stride<1, 1>(static_cast<int>(n)) * 4);
+    }
     if (io == 2) {
         const int64_t T = n / radix;
         const int64_t slot = fft_tma_slot_elems(pad, n, spb);
@@ -635,7 +760,7 @@ int fft_launch(const bplg_plan &p, const void *in, void *out, int64_t n, int64_t
     int spb = p.spb;
     if (p.io == 2) {
         int64_t ntiles = li.blocks;
-        int slot_elems = fft_tma_slot_elems(p.smem_pad, n, p.spb);
+        int slot_elems = fft_tma_slot_elems_layout(p.smem_layout, p.smem_pad, n, p.spb);
         int64_t grid = 0;
         rc = persistent_grid(li.func, li.threads, li.smem, ntiles, &grid);
         if (rc != BPLG_OK) return rc;

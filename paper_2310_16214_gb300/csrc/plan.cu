@@ -95,7 +95,9 @@ bool plan_structurally_valid(const bplg_plan &p, int dtype, int64_t n, std::stri
             if (n < 2) return fail(why, "FFT: n >= 2");
             if (p.smem_layout < 0 || p.smem_layout > 1 || p.smem_pad < 0 || p.smem_pad > 1 || p.io < 0 || p.io > 2)
                 return fail(why, "FFT: layout/pad/io out of range");
-            if (p.smem_layout == 1 && p.io != 0) return fail(why, "FFT: staged and pipelined io need the interleaved layout");
+            if (p.smem_layout == 1 && p.io == 1) return fail(why, "FFT: staged io needs the interleaved layout");
+            if (p.smem_layout == 1 && p.io == 2 && (p.radix != 16 || p.smem_pad != 1 || n < 1024 || n > 16384))
+                return fail(why, "FFT: the split-exchange pipelined variant is radix 16, padded, 1024 <= n <= 16384");
             return true;
         case BPLG_OP_FFT_TC:
             if (p.radix != 16 || p.P != 16) return fail(why, "tensor-core FFT: radix and P are 16");

@@ -462,20 +462,45 @@ int tune_search(const std::vector<bplg_plan> &plans, const std::vector<int> &reg
         int n0 = static_cast<int>(std::ceil(0.6 * std::sqrt(static_cast<double>(N))));
         n0 = std::max(5, std::min(n0, 24));
         n0 = std::min(std::min(n0, N), budget);
-        // seeded initial sample without replacement
+        // initial design: space-filling over the encoded knobs (the role of
+        // the Latin-hypercube start of GPTune): a seeded random first plan,
+        // then each next plan the one farthest from those already chosen
+        // (largest minimum squared distance; ties broken by a seeded random
+        // order).  Every categorical value and both ends of every numeric
+        // knob are then reached early instead of by chance.
+        const auto X = encode(plans);
         std::vector<int> perm(N);
         std::iota(perm.begin(), perm.end(), 0);
         for (int i = N - 1; i > 0; --i) {
             int j = static_cast<int>(rng.next() % uint64_t(i + 1));
             std::swap(perm[i], perm[j]);
         }
+        std::vector<double> dmin(N, INFINITY);
         double best = INFINITY;
         int since = 0;
+        int next = perm[0];
         for (int k = 0; k < n0; ++k) {
-            double t = evaluate(perm[k]);
+            double t = evaluate(next);
             if (t < best) best = t;
+            int far = -1;
+            double far_d = -1.0;
+            for (int q = 0; q < N; ++q) {
+                const int i = perm[q];
+                if (seen[i]) continue;
+                double d2 = 0.0;
+                for (size_t f = 0; f < X[i].size(); ++f) {
+                    const double u = X[i][f] - X[next][f];
+                    d2 += u * u;
+                }
+                dmin[i] = std::min(dmin[i], d2);
+                if (dmin[i] > far_d) {
+                    far_d = dmin[i];
+                    far = i;
+                }
+            }
+            if (far < 0) break;
+            next = far;
         }
-        const auto X = encode(plans);
         while (r.evaluations < budget && r.evaluations < N && since < 5) {
             // training set: log time, invalid points at a high penalty
             std::vector<std::vector<double>> Xs;
