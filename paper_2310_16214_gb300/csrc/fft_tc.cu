@@ -25,6 +25,7 @@
 #include "device_util.cuh"
 #include "fft_common.cuh"
 #include "internal.h"
+#include "tcgen05.cuh"
 
 namespace bplg {
 
@@ -264,31 +265,270 @@ __global__ void __launch_bounds__(MAXT)
     }
 }
 
+// ---------------------------------------------------------------------------
+// tcgen05 variant (io 0).  One thread per butterfly, as in the float32 path:
+// each thread holds its 16 inputs, multiplies them by the stage twiddles in
+// float32, splits them into 16-bit hi and lo parts and writes its row of
+// the A matrices [Re x_0..15 | Im x_0..15] (K = 32) to shared memory in the
+// no-swizzle K-major layout.  One thread then issues, per tile of 128
+// butterflies, the three split products A_lo B_hi + A_hi B_lo + A_hi B_hi
+// as 2 x 3 tcgen05.mma (M = 128, N = 32, K = 16) accumulating in float32 in
+// tensor memory, and commits them to an mbarrier; every thread reads its row
+// of the result back with one tcgen05.ld (32 columns: Re Y_0..15, Im
+// Y_0..15).  B is the real form of the 16-point DFT matrix,
+//     [Re Y | Im Y] = [Re x | Im x] [[C, dir S], [-dir S, C]],
+// C = cos(2 pi k n / 16), S = sin(2 pi k n / 16), also split into hi + lo.
+// The A matrices reuse the exchange buffer (dead while the MMAs run); the
+// exchanges between stages, the twiddles and the mixed-radix first stage are
+// those of the size-specialised float32 kernel.
+template <int PREC>
+struct TcSplit;
+
+template <>
+struct TcSplit<BPLG_TC_BF16> {
+    static constexpr uint32_t kFmt = 1;
+    static constexpr float kStageScale = 1.0f;
+    static __device__ __forceinline__ void pack(float x0, float x1, uint32_t &hi, uint32_t &lo) {
+        Split<BPLG_TC_BF16>::pack(x0, x1, hi, lo);
+    }
+};
+
+template <>
+struct TcSplit<BPLG_TC_F16> {
+    static constexpr uint32_t kFmt = 0;
+    static constexpr float kStageScale = 0.25f;
+    static __device__ __forceinline__ void pack(float x0, float x1, uint32_t &hi, uint32_t &lo) {
+        Split<BPLG_TC_F16>::pack(x0, x1, hi, lo);
+    }
+};
+
+struct Tc5Ctx {
+    unsigned char *abase;  // A hi (tiles x 8 KB), then A lo (tiles x 8 KB): aliases the exchange buffer
+    unsigned char *bsm;    // B hi (2 KB), B lo (2 KB)
+    uint64_t *bar;
+    uint32_t tmem;
+    int tiles;
+    uint32_t phase;
+    bool ok;
+};
+
+// The tensor-core 16-point DFT of every thread's v (in place).
+template <int PREC>
+__device__ __forceinline__ bool tc5_dft(float2 (&v)[16], Tc5Ctx &c) {
+    const int tid = threadIdx.x;
+    const int t = tid >> 7, row = tid & 127;
+    __syncthreads();  // the exchange buffer's last reads are done: A may overwrite it
+    {
+        unsigned char *ah = c.abase + t * 8192 + umma_canon_offset(row, 0);
+        unsigned char *al = ah + c.tiles * 8192;
+#pragma unroll
+        for (int kc = 0; kc < 4; ++kc) {  // 8 values per 16-byte chunk
+            uint32_t h[4], l[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int m0 = (kc & 1) * 8 + 2 * q;
+                const float x0 = kc < 2 ? v[m0].x : v[m0].y;
+                const float x1 = kc < 2 ? v[m0 + 1].x : v[m0 + 1].y;
+                TcSplit<PREC>::pack(x0, x1, h[q], l[q]);
+            }
+            *reinterpret_cast<uint4 *>(ah + kc * kUmmaLbo) = make_uint4(h[0], h[1], h[2], h[3]);
+            *reinterpret_cast<uint4 *>(al + kc * kUmmaLbo) = make_uint4(l[0], l[1], l[2], l[3]);
+        }
+    }
+    fence_proxy_async();  // the A rows are read by the tensor cores (async proxy)
+    tc_fence_before();
+    __syncthreads();
+    if (tid == 0) {
+        tc_fence_after();
+        constexpr uint32_t idesc = umma_idesc_f16(TcSplit<PREC>::kFmt, 128, 32);
+        const uint32_t a0 = smem_u32(c.abase), b0 = smem_u32(c.bsm);
+        for (int tt = 0; tt < c.tiles; ++tt) {
+            const uint32_t d = c.tmem + static_cast<uint32_t>(tt * 32);
+#pragma unroll
+            for (int ks = 0; ks < 2; ++ks) {
+                const uint32_t koff = ks * 2 * kUmmaLbo;
+                const uint64_t ahi = umma_smem_desc(a0 + tt * 8192 + koff);
+                const uint64_t alo = umma_smem_desc(a0 + c.tiles * 8192 + tt * 8192 + koff);
+                const uint64_t bhi = umma_smem_desc(b0 + koff);
+                const uint64_t blo = umma_smem_desc(b0 + 2048 + koff);
+                umma_f16(d, alo, bhi, idesc, ks);  // the first product of a tile overwrites D
+                umma_f16(d, ahi, blo, idesc, 1);
+                umma_f16(d, ahi, bhi, idesc, 1);
+            }
+        }
+        umma_commit(c.bar);
+    }
+    const bool done = __syncthreads_and(mbar_wait_bounded(c.bar, c.phase));
+    if (!done) {
+        c.ok = false;
+        return false;
+    }
+    c.phase ^= 1u;
+    tc_fence_after();
+    uint32_t r[32];
+    tmem_ld32(c.tmem + (static_cast<uint32_t>(tid & 96) << 16) + static_cast<uint32_t>(t * 32), r);
+    tmem_wait_ld();
+    tc_fence_before();  // ordered before the next barrier (the next stage's MMAs rewrite D)
+#pragma unroll
+    for (int n = 0; n < 16; ++n) v[n] = make_float2(__uint_as_float(r[n]), __uint_as_float(r[16 + n]));
+    return true;
+}
+
+template <int PREC, int LOGN, int DIR, int ST>
+__device__ __forceinline__ void tc5_stages(float2 (&v)[16], float2 *xbuf, int j, const float2 *__restrict__ tw,
+                                           float2 *gout, bool active, Tc5Ctx &c, float unscale) {
+    using S = FftShape<16, LOGN>;
+    using O = StageOut<16, LOGN, ST>;
+    constexpr int G = 16;
+    if constexpr (O::kMixed) {
+        first_stage_mixed<16, (1 << S::LR0), DIR>(v);
+    } else {
+        constexpr int LNS = O::LNS;
+        constexpr float sc = TcSplit<PREC>::kStageScale;
+        if constexpr (LNS > 0) {
+            const int k = j & ((1 << LNS) - 1);
+            const float2 *twk = tw + ((1 << LNS) << 4);
+#pragma unroll
+            for (int r = 0; r < 16; ++r) {
+                float2 w = r ? __ldg(twk + r * k) : make_float2(1.f, 0.f);
+                if (DIR > 0) w.y = -w.y;
+                v[r] = cmul(v[r], make_float2(w.x * sc, w.y * sc));
+            }
+        } else if constexpr (sc != 1.0f) {
+#pragma unroll
+            for (int r = 0; r < 16; ++r) v[r] = make_float2(v[r].x * sc, v[r].y * sc);
+        }
+        if (!tc5_dft<PREC>(v, c)) return;
+    }
+    const int ob = O::base(j);
+    if constexpr (ST == S::NST - 1) {
+        if (active) {
+#pragma unroll
+            for (int r = 0; r < 16; ++r)
+                __stcs(gout + ob + O::off(r), make_float2(v[r].x * unscale, v[r].y * unscale));
+        }
+    } else {
+        const int pb = pad_g<G>(ob);
+        const int pj = pad_g<G>(j);
+        constexpr int TP = S::T + S::T / G;
+        __syncthreads();  // (mixed stage) earlier readers of the buffer are done
+#pragma unroll
+        for (int r = 0; r < 16; ++r) xbuf[pb + O::off(r) + O::off(r) / G] = v[r];
+        __syncthreads();
+#pragma unroll
+        for (int m = 0; m < 16; ++m) v[m] = xbuf[pj + m * TP];
+        tc5_stages<PREC, LOGN, DIR, ST + 1>(v, xbuf, j, tw, gout, active, c, unscale);
+    }
+}
+
+template <int PREC, int LOGN, int DIR, int MAXT>
+__global__ void __launch_bounds__(MAXT)
+    fft_tc5_kernel(const float2 *in, float2 *out, const float2 *__restrict__ tw, int logn, int spb, int64_t batch) {
+    using S = FftShape<16, LOGN>;
+    constexpr int N = 1 << LOGN;
+    constexpr int STRIDE = N + N / 16;
+    (void)logn;
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    __shared__ __align__(8) uint64_t bar;
+    __shared__ uint32_t tmem_slot;
+    const int tid = threadIdx.x;
+    const int tiles = blockDim.x >> 7;
+    const uint32_t ncols = tiles <= 1 ? 32u : (tiles <= 2 ? 64u : (tiles <= 4 ? 128u : 256u));
+    const int s = tid >> S::LOGT;
+    const int j = tid & (S::T - 1);
+    const int64_t sig = static_cast<int64_t>(blockIdx.x) * spb + s;
+    const bool active = sig < batch;
+    unsigned char *bsm = smem_raw;
+    float2 *xall = reinterpret_cast<float2 *>(smem_raw + 4096);
+
+    if (tid < 32) {
+        tmem_alloc(&tmem_slot, ncols);
+        tmem_relinquish();
+    }
+    if (tid == 0) {
+        mbar_init(&bar, 1);
+        fence_mbar_init();
+    }
+    // B = real 32 x 32 DFT matrix, stored as rows n (output column) of K = 32
+    for (int e = tid; e < 32 * 32; e += blockDim.x) {
+        const int n = e >> 5, k = e & 31;
+        const int th = ((k & 15) * (n & 15)) & 15;
+        const float cs = cos16(th), sn = DIR * sin16(th);
+        const float val = (k < 16) ? (n < 16 ? cs : sn) : (n < 16 ? -sn : cs);
+        uint32_t h, l;
+        TcSplit<PREC>::pack(val, 0.f, h, l);
+        *reinterpret_cast<uint16_t *>(bsm + umma_canon_offset(n, k)) = static_cast<uint16_t>(h & 0xFFFFu);
+        *reinterpret_cast<uint16_t *>(bsm + 2048 + umma_canon_offset(n, k)) = static_cast<uint16_t>(l & 0xFFFFu);
+    }
+    fence_proxy_async();
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    Tc5Ctx c{smem_raw + 4096, bsm, &bar, tmem_slot, tiles, 0u, true};
+
+    float2 v[16];
+    const float2 *g = in + sig * N + j;
+#pragma unroll
+    for (int m = 0; m < 16; ++m) v[m] = active ? __ldcs(g + m * S::T) : make_float2(0.f, 0.f);
+    constexpr int tc_stages = LOGN / 4;
+    float unscale = 1.f;
+#pragma unroll
+    for (int q = 0; q < tc_stages; ++q) unscale *= 1.0f / TcSplit<PREC>::kStageScale;
+    tc5_stages<PREC, LOGN, DIR, 0>(v, xall + s * STRIDE, j, tw, out + sig * N, active, c, unscale);
+
+    tc_fence_before();
+    __syncthreads();
+    if (!c.ok && tid == 0) mbar_wait_bounded(&bar, c.phase);  // let a late commit land before freeing
+    if (tid < 32) tmem_dealloc(c.tmem, ncols);
+}
+
 namespace {
 
+template <int PREC, int DIR, int MAXT>
+const void *tc5_func_t(int logn) {
+    switch (logn) {
+        case 10: return reinterpret_cast<const void *>(&fft_tc5_kernel<PREC, 10, DIR, MAXT>);
+        case 11: return reinterpret_cast<const void *>(&fft_tc5_kernel<PREC, 11, DIR, MAXT>);
+        case 12: return reinterpret_cast<const void *>(&fft_tc5_kernel<PREC, 12, DIR, MAXT>);
+        case 13: return reinterpret_cast<const void *>(&fft_tc5_kernel<PREC, 13, DIR, MAXT>);
+        case 14: return reinterpret_cast<const void *>(&fft_tc5_kernel<PREC, 14, DIR, MAXT>);
+        default: return nullptr;
+    }
+}
+
 template <int PREC, int DIR>
-const void *tc_func_pd(int threads) {
+const void *tc_func_pd(int threads, int io, int logn) {
+    if (io == 0) {
+        if (threads % 128 != 0) return nullptr;
+        return threads <= 512 ? tc5_func_t<PREC, DIR, 512>(logn) : tc5_func_t<PREC, DIR, 1024>(logn);
+    }
     if (threads <= 512) return reinterpret_cast<const void *>(&fft_tc_kernel<PREC, DIR, 512>);
     return reinterpret_cast<const void *>(&fft_tc_kernel<PREC, DIR, 1024>);
 }
 
-const void *tc_func(int prec, int dir, int threads) {
-    if (prec == BPLG_TC_BF16) return dir < 0 ? tc_func_pd<BPLG_TC_BF16, -1>(threads) : tc_func_pd<BPLG_TC_BF16, 1>(threads);
-    if (prec == BPLG_TC_F16) return dir < 0 ? tc_func_pd<BPLG_TC_F16, -1>(threads) : tc_func_pd<BPLG_TC_F16, 1>(threads);
+const void *tc_func(int prec, int dir, int threads, int io, int logn) {
+    if (prec == BPLG_TC_BF16)
+        return dir < 0 ? tc_func_pd<BPLG_TC_BF16, -1>(threads, io, logn) : tc_func_pd<BPLG_TC_BF16, 1>(threads, io, logn);
+    if (prec == BPLG_TC_F16)
+        return dir < 0 ? tc_func_pd<BPLG_TC_F16, -1>(threads, io, logn) : tc_func_pd<BPLG_TC_F16, 1>(threads, io, logn);
     return nullptr;
 }
 
 }  // namespace
 
-int fft_tc_smem_bytes(int64_t n, int spb) { return spb * sig_stride<0, 1>(static_cast<int>(n)) * 8; }
+// io 1 (mma.sync): the padded exchange tile; io 0 (tcgen05): the B matrices
+// (hi and lo, 4 KB) and the padded exchange tile, which the A matrices reuse
+int fft_tc_smem_bytes(int64_t n, int spb, int io) {
+    return (io == 0 ? 4096 : 0) + spb * sig_stride<0, 1>(static_cast<int>(n)) * 8;
+}
 
 bool fft_tc_launch_info(const bplg_plan &p, int64_t n, int64_t batch, int prec, int dir, Launch *out) {
     if (!plan_structurally_valid(p, BPLG_F32, n, nullptr)) return false;
-    const void *f = tc_func(prec, dir, p.L);
+    const void *f = tc_func(prec, dir, p.L, p.io, ilog2(n));
     if (!f) return false;
     out->func = f;
     out->threads = p.L;
-    out->smem = fft_tc_smem_bytes(n, p.spb);
+    out->smem = fft_tc_smem_bytes(n, p.spb, p.io);
     out->blocks = (batch + p.spb - 1) / p.spb;
     return true;
 }
@@ -309,6 +549,21 @@ int fft_tc_launch(const bplg_plan &p, const void *in, void *out, int64_t n, int6
     cudaError_t e = cudaLaunchKernel(li.func, dim3(static_cast<unsigned>(li.blocks)), dim3(li.threads), args,
                                      static_cast<size_t>(li.smem), s);
     return e == cudaSuccess ? BPLG_OK : launch_error(e, "fft tc launch", li.func, li.blocks, li.threads, li.smem);
+}
+
+// Read (and optionally clear) the device error word of this file's kernels
+// (the tcgen05 kernel's bounded mbarrier waits) on the current device.
+int fft_tc_device_status(int *flag, bool reset) {
+    int v = 0;
+    cudaError_t e = cudaMemcpyFromSymbol(&v, g_device_error, sizeof(int));
+    if (e != cudaSuccess) return cuda_error(e, "device status");
+    if (reset && v) {
+        const int zero = 0;
+        e = cudaMemcpyToSymbol(g_device_error, &zero, sizeof(int));
+        if (e != cudaSuccess) return cuda_error(e, "device status reset");
+    }
+    *flag = v;
+    return BPLG_OK;
 }
 
 }  // namespace bplg

@@ -17,7 +17,7 @@
 namespace bplg {
 
 int fft_smem_bytes(int radix, int layout, int pad, int io, int64_t n, int spb);
-int fft_tc_smem_bytes(int64_t n, int spb);
+int fft_tc_smem_bytes(int64_t n, int spb, int io);
 bool fft_tc_launch_info(const bplg_plan &p, int64_t n, int64_t batch, int prec, int dir, Launch *out);
 int tridiag_smem_bytes(int pad, int64_t n, int spb, bool refined, int layout, int io, int log_m, int P);
 
@@ -102,8 +102,10 @@ bool plan_structurally_valid(const bplg_plan &p, int dtype, int64_t n, std::stri
         case BPLG_OP_FFT_TC:
             if (p.radix != 16 || p.P != 16) return fail(why, "tensor-core FFT: radix and P are 16");
             if (n < 512) return fail(why, "tensor-core FFT: n >= 512 (a warp per 32 butterflies)");
-            if (p.smem_pad != 1 || p.smem_layout != 0 || p.io != 1)
-                return fail(why, "tensor-core FFT: padded interleaved layout, staged io");
+            if (p.smem_pad != 1 || p.smem_layout != 0 || p.io < 0 || p.io > 1)
+                return fail(why, "tensor-core FFT: padded interleaved layout; io 0 (tcgen05) or 1 (mma.sync)");
+            if (p.io == 0 && (n < 1024 || n > 16384 || p.L % 128 != 0))
+                return fail(why, "tensor-core FFT with tcgen05: 1024 <= n <= 16384 and blocks of 128-thread tiles");
             return true;
         case BPLG_OP_TRIDIAG:
         case BPLG_OP_TRIDIAG_REFINED: {
@@ -141,7 +143,7 @@ int plan_smem_bytes(const bplg_plan &p, int dtype, int64_t n) {
     switch (p.op) {
         case BPLG_OP_SCAN: return 0;
         case BPLG_OP_FFT: return fft_smem_bytes(p.radix, p.smem_layout, p.smem_pad, p.io, n, p.spb);
-        case BPLG_OP_FFT_TC: return fft_tc_smem_bytes(n, p.spb);
+        case BPLG_OP_FFT_TC: return fft_tc_smem_bytes(n, p.spb, p.io);
         case BPLG_OP_TRIDIAG:
             return tridiag_smem_bytes(p.smem_pad, n, p.spb, false, p.smem_layout, p.io, ilog2(p.cr_switch), p.P);
         case BPLG_OP_TRIDIAG_REFINED:
@@ -170,7 +172,8 @@ void plan_finalize(bplg_plan *p, int dtype, int64_t n) {
         case BPLG_OP_FFT_TC:
             p->radix = p->P;
             p->shuffle = p->pattern = p->cr_switch = p->smem_layout = 0;
-            p->smem_pad = p->io = 1;
+            p->smem_pad = 1;
+            if (p->io != 0) p->io = 1;
             p->S = static_cast<int32_t>(p->spb * n);
             break;
         case BPLG_OP_TRIDIAG:
@@ -213,7 +216,10 @@ std::vector<bplg_plan> enumerate_structural(int op, int dtype, int64_t n) {
             } else if (op == BPLG_OP_FFT_TC) {
                 if (P != 16) continue;
                 p.radix = 16;
-                push(p);
+                for (int io = 0; io <= 1; ++io) {
+                    p.io = io;
+                    push(p);
+                }
             } else if (op == BPLG_OP_FFT) {
                 if (P < 2 || P > 16) continue;
                 p.radix = P;

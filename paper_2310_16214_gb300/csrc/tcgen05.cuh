@@ -1,0 +1,102 @@
+// Fifth-generation tensor-core building blocks (sm_100 family, used on
+// sm_103a): tensor-memory allocation, tcgen05.mma from shared-memory matrix
+// descriptors with the accumulator in tensor memory, commit to an mbarrier,
+// and tensor-memory loads.  Inline PTX only.
+//
+// Operand layout used here: K-major, no swizzle.  A matrix of R rows and
+// K = 32 16-bit columns is stored as "core matrices" of 8 rows x 16 bytes
+// (8 elements), each core matrix 128 contiguous bytes (row r of the core at
+// byte 16 r); core matrices adjacent along K are LBO = 128 bytes apart and
+// core matrices adjacent along the rows (the next 8 rows) SBO = 512 bytes
+// apart.  Element (row, k) is therefore at byte
+//     (row / 8) * 512 + (k / 8) * 128 + (row % 8) * 16 + (k % 8) * 2,
+// and one MMA's K = 16 slice starting at k0 starts k0 / 8 * 128 bytes in.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "tma.cuh"
+
+namespace bplg {
+
+constexpr uint32_t kUmmaLbo = 128;  // bytes between core matrices along K
+constexpr uint32_t kUmmaSbo = 512;  // bytes between 8-row groups (K = 32)
+
+__host__ __device__ constexpr uint32_t umma_canon_offset(int row, int k) {
+    return static_cast<uint32_t>((row >> 3) * kUmmaSbo + (k >> 3) * kUmmaLbo + (row & 7) * 16 + (k & 7) * 2);
+}
+
+// Shared-memory matrix descriptor: start address, leading- and stride-
+// dimension byte offsets (all >> 4), descriptor version 1, no swizzle.
+__device__ __forceinline__ uint64_t umma_smem_desc(uint32_t smem_addr) {
+    uint64_t d = 0;
+    d |= static_cast<uint64_t>((smem_addr >> 4) & 0x3FFFu);
+    d |= static_cast<uint64_t>((kUmmaLbo >> 4) & 0x3FFFu) << 16;
+    d |= static_cast<uint64_t>((kUmmaSbo >> 4) & 0x3FFFu) << 32;
+    d |= static_cast<uint64_t>(1) << 46;  // version
+    return d;                             // base offset 0, layout type 0 (no swizzle)
+}
+
+// Instruction descriptor of kind::f16: float32 accumulator, A and B of the
+// same 16-bit type (fmt 0 = f16, 1 = bf16), both K-major, M x N tile.
+__host__ __device__ constexpr uint32_t umma_idesc_f16(uint32_t fmt, int M, int N) {
+    return (1u << 4) | (fmt << 7) | (fmt << 10) | (static_cast<uint32_t>(N >> 3) << 17) |
+           (static_cast<uint32_t>(M >> 4) << 24);
+}
+
+// Allocate ncols (a power of two >= 32) tensor-memory columns; one full
+// warp executes it and the address lands in *dst (shared memory).
+__device__ __forceinline__ void tmem_alloc(uint32_t *dst, uint32_t ncols) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(dst)),
+                 "r"(ncols)
+                 : "memory");
+}
+
+__device__ __forceinline__ void tmem_relinquish() {
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+
+// D[tmem] (+)= A[smem] * B[smem]; accumulate = 0 overwrites D.
+__device__ __forceinline__ void umma_f16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                         uint32_t accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}"
+        ::"r"(d_tmem), "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+
+// One arrival on `bar` once every tcgen05.mma this thread issued has completed.
+__device__ __forceinline__ void umma_commit(uint64_t *bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// 32 consecutive 32-bit columns of one tensor-memory lane per thread: lane =
+// the warp's 32-lane quarter + laneid (taddr carries the quarter's first lane
+// in bits 16..31 and the first column in bits 0..15).
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+        "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+        "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr)
+        : "memory");
+}
+
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+}  // namespace bplg

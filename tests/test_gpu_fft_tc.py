@@ -1,6 +1,7 @@
 """Tensor-core FFT (radix-16 stages as split hi/lo BF16 or FP16 MMA with
 float32 accumulation) against the float64 oracle: relative L2 error per
-signal <= 1e-5 * log2 N, forward and inverse, every plan, both precisions."""
+signal <= 1e-5 * log2 N, forward and inverse, every plan (the tcgen05
+kernels, io 0, and the mma.sync kernels, io 1), both precisions."""
 import math
 
 import numpy as np
@@ -40,6 +41,8 @@ def test_every_plan(bp, n, prec):
     refs = {d: oracle.fft(z, d) for d in (-1, 1)}
     plans = bp.enumerate_plans(bp.OP_FFT_TC, bp.F32, n)
     assert plans
+    # the tcgen05 kernels (io 0) are in the space from n = 1024 on
+    assert any(p.io == 0 for p in plans) == (n >= 1024)
     for p in plans:
         for d in (-1, 1):
             err = fft_rel_err(run(bp, z, d, prec, p), refs[d]).max()
@@ -56,6 +59,16 @@ def test_precision_configuration_sampled(bp, n):
     for prec in (0, 1):
         X = run(bp, z, -1, prec)
         assert fft_rel_err(X[rows], ref).max() <= 1e-5 * math.log2(n)
+
+
+def test_tcgen05_plans_leave_no_device_error(bp):
+    n, batch = 4096, 7
+    z = si.fft_c64(batch, n, stream=611)
+    ref = oracle.fft(z, -1)
+    for p in bp.enumerate_plans(bp.OP_FFT_TC, bp.F32, n):
+        if p.io == 0:
+            assert fft_rel_err(run(bp, z, -1, 1, p), ref).max() <= 1e-5 * math.log2(n), p
+    assert bp.device_status() == 0
 
 
 def test_argument_errors(bp):
