@@ -302,6 +302,12 @@ struct TcSplit<BPLG_TC_F16> {
     }
 };
 
+// cos(2 pi e / 16), e = 0..15, as a table (the B matrix is built per block
+// with data-dependent indices); sin(2 pi e / 16) = cos(2 pi (e - 4) / 16)
+__device__ const float kCos16Table[16] = {cos16(0),  cos16(1),  cos16(2),  cos16(3),  cos16(4),  cos16(5),
+                                          cos16(6),  cos16(7),  cos16(8),  cos16(9),  cos16(10), cos16(11),
+                                          cos16(12), cos16(13), cos16(14), cos16(15)};
+
 struct Tc5Ctx {
     unsigned char *abase;  // A hi (tiles x 8 KB), then A lo (tiles x 8 KB): aliases the exchange buffer
     unsigned char *bsm;    // B hi (2 KB), B lo (2 KB)
@@ -358,7 +364,11 @@ __device__ __forceinline__ bool tc5_dft(float2 (&v)[16], Tc5Ctx &c) {
         }
         umma_commit(c.bar);
     }
-    const bool done = __syncthreads_and(mbar_wait_bounded(c.bar, c.phase));
+    // one warp polls the mbarrier; the others wait at the barrier without
+    // issuing instructions
+    bool arrived = true;
+    if (tid < 32) arrived = mbar_wait_bounded(c.bar, c.phase);
+    const bool done = __syncthreads_and(arrived);
     if (!done) {
         c.ok = false;
         return false;
@@ -384,19 +394,15 @@ __device__ __forceinline__ void tc5_stages(float2 (&v)[16], float2 *xbuf, int j,
         first_stage_mixed<16, (1 << S::LR0), DIR>(v);
     } else {
         constexpr int LNS = O::LNS;
-        constexpr float sc = TcSplit<PREC>::kStageScale;
         if constexpr (LNS > 0) {
             const int k = j & ((1 << LNS) - 1);
             const float2 *twk = tw + ((1 << LNS) << 4);
 #pragma unroll
-            for (int r = 0; r < 16; ++r) {
-                float2 w = r ? __ldg(twk + r * k) : make_float2(1.f, 0.f);
+            for (int r = 1; r < 16; ++r) {
+                float2 w = __ldg(twk + r * k);
                 if (DIR > 0) w.y = -w.y;
-                v[r] = cmul(v[r], make_float2(w.x * sc, w.y * sc));
+                v[r] = cmul(v[r], w);
             }
-        } else if constexpr (sc != 1.0f) {
-#pragma unroll
-            for (int r = 0; r < 16; ++r) v[r] = make_float2(v[r].x * sc, v[r].y * sc);
         }
         if (!tc5_dft<PREC>(v, c)) return;
     }
@@ -449,11 +455,14 @@ __global__ void __launch_bounds__(MAXT)
         mbar_init(&bar, 1);
         fence_mbar_init();
     }
-    // B = real 32 x 32 DFT matrix, stored as rows n (output column) of K = 32
+    // B = real 32 x 32 DFT matrix times the stage scale (FP16: 1/4, exact,
+    // keeps the outputs' growth inside the 16-bit range), stored as rows n
+    // (output column) of K = 32
     for (int e = tid; e < 32 * 32; e += blockDim.x) {
         const int n = e >> 5, k = e & 31;
         const int th = ((k & 15) * (n & 15)) & 15;
-        const float cs = cos16(th), sn = DIR * sin16(th);
+        constexpr float sc = TcSplit<PREC>::kStageScale;
+        const float cs = kCos16Table[th] * sc, sn = DIR * kCos16Table[(th + 12) & 15] * sc;
         const float val = (k < 16) ? (n < 16 ? cs : sn) : (n < 16 ? -sn : cs);
         uint32_t h, l;
         TcSplit<PREC>::pack(val, 0.f, h, l);
