@@ -803,6 +803,72 @@ def tune_report(args):
     print(json.dumps({"tune_report": summary}))
 
 
+def uneven_report(args):
+    """The uneven batch (4096 int32 scans + 4096 FFTs + 4096 tridiagonal
+    systems, sizes 2^U{5..13}) as one graph launch, against the same problems
+    run as one batched launch per (operation, size) class with a plan tuned by
+    the learned tuner for that class (budget 16), the launches back to back on
+    one stream.  Median of `reps` runs each."""
+    import torch
+    torch.cuda.set_device(0)
+    import paper_2310_16214_gb300 as bp
+    dev = torch.device("cuda", 0)
+    st = torch.cuda.current_stream()
+    count = UNEVEN_COUNT
+    seed = si.CONFIG_SEEDS["uneven"]
+    ns = [int(v) for v in si.uneven_sizes(3 * count, seed)]
+    wl = Workload(torch, bp, dev, rows=["uneven"], plans="query")
+    graph = wl.items[0]["fn"]
+    classes = {}
+    for k, n in enumerate(ns):
+        op = ("scan", "fft", "tridiag")[k // count]
+        classes[(op, n)] = classes.get((op, n), 0) + 1
+    launches = []
+    for (op, n), b in sorted(classes.items()):
+        if op == "scan":
+            xin = torch.randint(-1000, 1001, (b * n,), device=dev, dtype=torch.int32)
+            xout = torch.empty_like(xin)
+            p, _ = bp.tune_plan(bp.OP_SCAN, bp.I32, n, b, bp.TUNE_LEARNED, budget=16, seed=args.seed)
+            launches.append(lambda xin=xin, xout=xout, n=n, b=b, p=p: bp.scan_batched(xin, xout, n, b, dtype=bp.I32,
+                                                                                     plan=p))
+        elif op == "fft":
+            zin = torch.rand(2 * b * n, device=dev) * 2 - 1
+            zout = torch.empty_like(zin)
+            p, _ = bp.tune_plan(bp.OP_FFT, bp.F32, n, b, bp.TUNE_LEARNED, budget=16, seed=args.seed)
+            launches.append(lambda zin=zin, zout=zout, n=n, b=b, p=p: bp.fft_batched(zin, zout, n, b, -1, plan=p))
+        else:
+            a, bb, c, d, _ = si.tridiag_f32(b, n, stream=700 + n)
+            ts = [torch.from_numpy(v).to(dev) for v in (a, bb, c, d)]
+            x = torch.empty_like(ts[0])
+            p, _ = bp.tune_plan(bp.OP_TRIDIAG, bp.F32, n, b, bp.TUNE_LEARNED, budget=16, seed=args.seed)
+            launches.append(lambda ts=ts, x=x, n=n, b=b, p=p: bp.tridiag_batched(*ts, x, n, b, plan=p))
+
+    def timeit(fn):
+        for _ in range(3):
+            fn()
+        evs = []
+        for _ in range(args.reps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(st)
+            fn()
+            e1.record(st)
+            evs.append((e0, e1))
+        torch.cuda.synchronize()
+        return statistics.median(a.elapsed_time(b) for a, b in evs)
+
+    def all_batched():
+        for f in launches:
+            f()
+
+    g_ms = timeit(graph)
+    b_ms = timeit(all_batched)
+    row = {"uneven_report": {"items": 3 * count, "size_classes": len(classes), "graph_ms": round(g_ms, 5),
+                             "batched_per_class_ms": round(b_ms, 5), "graph_speedup": round(b_ms / g_ms, 3),
+                             "graph_gelem_s": round(sum(ns) / (g_ms * 1e-3) / 1e9, 2)}}
+    print(json.dumps(row), flush=True)
+    return row
+
+
 def precision_report(args):
     """Precision configuration: FFT N in {2^10, 2^12, 2^14}, batch 2^26/N,
     tensor-core radix-16 stages with BF16 and FP16 split operands against
@@ -870,6 +936,8 @@ def main():
     ap.add_argument("--tune-report", action="store_true", help="tuned vs exhaustive Phi report instead of the bench")
     ap.add_argument("--precision-report", action="store_true",
                     help="tensor-core (BF16/FP16 split) vs float32 FFT: error and time per N")
+    ap.add_argument("--uneven-report", action="store_true",
+                    help="the uneven batch's graph launch against one tuned batched launch per size class")
     ap.add_argument("--ops", default="", help="comma-separated ops for --tune-report")
     ap.add_argument("--reps", type=int, default=50)
     ap.add_argument("--bo-budget", type=int, default=40)
@@ -884,6 +952,8 @@ def main():
         tune_report(args)
     elif args.precision_report:
         precision_report(args)
+    elif args.uneven_report:
+        uneven_report(args)
     elif args.impl == "reference":
         run_reference(args)
     else:

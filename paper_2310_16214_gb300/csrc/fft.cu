@@ -32,6 +32,11 @@
 
 namespace bplg {
 
+// size-specialised kernels (fft_fixed_fwd.cu / fft_fixed_inv.cu); nullptr
+// when (radix, layout, threads, log2 n) has no instantiation
+const void *fft_fixed_lookup_fwd(int radix, int layout, int threads, int logn);
+const void *fft_fixed_lookup_inv(int radix, int layout, int threads, int logn);
+
 template <int R, int DIR, int LAYOUT, int PAD, int STAGED, int MAXT>
 __global__ void __launch_bounds__(MAXT)
     fft_kernel(const float2 *in, float2 *out, const float2 *__restrict__ tw, int logn, int spb,
@@ -159,32 +164,6 @@ __global__ void __launch_bounds__(MAXT)
             for (int r = 0; r < R; ++r) __stcs(g + om(r), v[r]);
         }
     }
-}
-
-// Size-specialised variant of fft_kernel (same plan, same arithmetic, same
-// shared-memory layout) for padded, directly loaded transforms of the large
-// sizes; its compile-time stage schedule (fft_fixed_stages) is described in
-// fft_common.cuh.
-template <int R, int LOGN, int DIR, int LAYOUT, int MAXT>
-__global__ void __launch_bounds__(MAXT)
-    fft_fixed_kernel(const float2 *in, float2 *out, const float2 *__restrict__ tw, int logn, int spb,
-                     int64_t batch) {
-    using S = FftShape<R, LOGN>;
-    (void)logn;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int tid = threadIdx.x;
-    const int s = tid >> S::LOGT;
-    const int j = tid & (S::T - 1);
-    const int64_t sig = static_cast<int64_t>(blockIdx.x) * spb + s;
-    const bool active = sig < batch;
-    const int sbase = s * sig_stride<LAYOUT, 1>(1 << LOGN);
-    float2 *buf2 = reinterpret_cast<float2 *>(smem_raw) + sbase;
-    float *buf1 = reinterpret_cast<float *>(smem_raw) + sbase;
-    const float2 *g = in + sig * (int64_t(1) << LOGN) + j;
-    float2 v[R];
-#pragma unroll
-    for (int m = 0; m < R; ++m) v[m] = active ? __ldcs(g + m * S::T) : make_float2(0.f, 0.f);
-    fft_fixed_stages<R, LOGN, DIR, LAYOUT, 0>(v, buf2, buf1, j, tw, out + sig * (int64_t(1) << LOGN), active);
 }
 
 // Persistent, TMA-pipelined variant (io = 2).  Grid = the resident-block
@@ -574,19 +553,6 @@ const void *fft_func_io_t(int io) {
     }
 }
 
-// Size-specialised kernels: radix 16, padded, direct io, n = 2^10 .. 2^14.
-template <int DIR, int LAYOUT, int MAXT>
-const void *fft_fixed_func(int logn) {
-    switch (logn) {
-        case 10: return reinterpret_cast<const void *>(&fft_fixed_kernel<16, 10, DIR, LAYOUT, MAXT>);
-        case 11: return reinterpret_cast<const void *>(&fft_fixed_kernel<16, 11, DIR, LAYOUT, MAXT>);
-        case 12: return reinterpret_cast<const void *>(&fft_fixed_kernel<16, 12, DIR, LAYOUT, MAXT>);
-        case 13: return reinterpret_cast<const void *>(&fft_fixed_kernel<16, 13, DIR, LAYOUT, MAXT>);
-        case 14: return reinterpret_cast<const void *>(&fft_fixed_kernel<16, 14, DIR, LAYOUT, MAXT>);
-        default: return nullptr;
-    }
-}
-
 template <int DIR, int MAXT>
 const void *fft_tma_fixed_func(int logn) {
     switch (logn) {
@@ -613,9 +579,14 @@ const void *fft_tma_split_func(int logn) {
 
 template <int R, int DIR, int LAYOUT, int PAD>
 const void *fft_func_io(int io, int threads, int logn) {
+    if constexpr ((R == 16 || R == 8) && PAD == 1) {
+        if (io == 0) {
+            const void *f = DIR < 0 ? fft_fixed_lookup_fwd(R, LAYOUT, threads, logn)
+                                    : fft_fixed_lookup_inv(R, LAYOUT, threads, logn);
+            if (f) return f;
+        }
+    }
     if constexpr (R == 16 && PAD == 1) {
-        if (io == 0 && logn >= 10 && logn <= 14)
-            return threads <= 512 ? fft_fixed_func<DIR, LAYOUT, 512>(logn) : fft_fixed_func<DIR, LAYOUT, 1024>(logn);
         if (LAYOUT == 0 && io == 2 && logn >= 10 && logn <= 14)
             return threads <= 512 ? fft_tma_fixed_func<DIR, 512>(logn) : fft_tma_fixed_func<DIR, 1024>(logn);
         if (LAYOUT == 1 && io == 2 && logn >= 10 && logn <= 14)

@@ -216,27 +216,26 @@ __device__ __forceinline__ void fft_fixed_stages(float2 (&v)[R], float2 *buf2, f
     } else {
         const int pb = pad_g<G>(ob);
         const int pj = pad_g<G>(j);
-        constexpr int TP = S::T + S::T / G;
         if constexpr (LAYOUT == 0) {
             __syncthreads();
 #pragma unroll
             for (int r = 0; r < R; ++r) buf2[pb + O::off(r) + O::off(r) / G] = v[r];
             __syncthreads();
 #pragma unroll
-            for (int m = 0; m < R; ++m) v[m] = buf2[pj + m * TP];
+            for (int m = 0; m < R; ++m) v[m] = buf2[pj + m * S::T + (m * S::T) / G];
         } else {
             __syncthreads();
 #pragma unroll
             for (int r = 0; r < R; ++r) buf1[pb + O::off(r) + O::off(r) / G] = v[r].x;
             __syncthreads();
 #pragma unroll
-            for (int m = 0; m < R; ++m) v[m].x = buf1[pj + m * TP];
+            for (int m = 0; m < R; ++m) v[m].x = buf1[pj + m * S::T + (m * S::T) / G];
             __syncthreads();
 #pragma unroll
             for (int r = 0; r < R; ++r) buf1[pb + O::off(r) + O::off(r) / G] = v[r].y;
             __syncthreads();
 #pragma unroll
-            for (int m = 0; m < R; ++m) v[m].y = buf1[pj + m * TP];
+            for (int m = 0; m < R; ++m) v[m].y = buf1[pj + m * S::T + (m * S::T) / G];
         }
         fft_fixed_stages<R, LOGN, DIR, LAYOUT, ST + 1>(v, buf2, buf1, j, tw, gout, active);
     }

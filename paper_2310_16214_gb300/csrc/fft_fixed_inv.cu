@@ -1,0 +1,10 @@
+// Size-specialised batched FFT kernels, inverse direction (see fft_fixed.cuh).
+#include "fft_fixed.cuh"
+
+namespace bplg {
+
+const void *fft_fixed_lookup_inv(int radix, int layout, int threads, int logn) {
+    return fft_fixed_lookup_dir<1>(radix, layout, threads, logn);
+}
+
+}  // namespace bplg

@@ -416,13 +416,12 @@ __device__ __forceinline__ void tc5_stages(float2 (&v)[16], float2 *xbuf, int j,
     } else {
         const int pb = pad_g<G>(ob);
         const int pj = pad_g<G>(j);
-        constexpr int TP = S::T + S::T / G;
         __syncthreads();  // (mixed stage) earlier readers of the buffer are done
 #pragma unroll
         for (int r = 0; r < 16; ++r) xbuf[pb + O::off(r) + O::off(r) / G] = v[r];
         __syncthreads();
 #pragma unroll
-        for (int m = 0; m < 16; ++m) v[m] = xbuf[pj + m * TP];
+        for (int m = 0; m < 16; ++m) v[m] = xbuf[pj + m * S::T + (m * S::T) / G];
         tc5_stages<PREC, LOGN, DIR, ST + 1>(v, xbuf, j, tw, gout, active, c, unscale);
     }
 }

@@ -120,8 +120,8 @@ bool plan_structurally_valid(const bplg_plan &p, int dtype, int64_t n, std::stri
             if (p.smem_layout < 0 || p.smem_layout > (p.op == BPLG_OP_TRIDIAG_REFINED ? 6 : 2))
                 return fail(why, "tridiag: smem_layout out of range (0 strided rows, 1 compacted levels, 2 register "
                                  "levels; refined: bit 0 float64 coefficients, bit 1 compacted levels, 4-6 register levels)");
-            if (p.op == BPLG_OP_TRIDIAG && p.smem_layout == 2 && (p.P < 2 || p.io != 0))
-                return fail(why, "tridiag: register levels need P >= 2 and the per-block kernel");
+            if (p.op == BPLG_OP_TRIDIAG && p.smem_layout == 2 && (p.P < 2 || (p.io == 1 && (p.P < 4 || n < 64))))
+                return fail(why, "tridiag: register levels need P >= 2 (P >= 4 and n >= 64 when pipelined)");
             if (p.op == BPLG_OP_TRIDIAG && p.smem_layout == 1 && (p.smem_pad != 1 || p.io != 0))
                 return fail(why, "tridiag: the compacted layout is always padded and per-block");
             if (p.op == BPLG_OP_TRIDIAG_REFINED && p.smem_layout < 4 && (p.smem_layout & 2) && p.smem_pad != 1)

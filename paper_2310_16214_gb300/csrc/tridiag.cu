@@ -321,6 +321,120 @@ __global__ void __launch_bounds__(MAXT)
                                         bnd);
 }
 
+// Register-level CR fed by bulk asynchronous copies (smem_layout 2, io 1).
+// A persistent block streams its tiles (spb systems) through one shared-
+// memory slot: 4 copies per tile (a, b, c, d, each the tile's contiguous
+// slice) complete on one mbarrier.  The slot is refilled as soon as every
+// thread holds its run in registers, so the next tile's copy overlaps this
+// tile's solve; one slot keeps the occupancy of the per-block kernel.  Each thread reads its P-run of the four arrays from the slot, the
+// slot is refilled at once, and the solve is tridiag_reg_kernel's.  Waits
+// are bounded: on timeout the block records an error, drains its own copies
+// (bounded) and returns.
+template <int P, int PAD, int SHUFFLE, int MAXT>
+__global__ void __launch_bounds__(MAXT)
+    tridiag_reg_tma_kernel(const float *ga, const float *gb, const float *gc, const float *gd, float *x, int logn,
+                           int log_m, int log_tps, int spb, int64_t batch, int64_t ntiles) {
+    constexpr int NS = 1;
+    static_assert(P >= 4, "16-byte runs");
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    __shared__ __align__(8) uint64_t full[NS];
+    const int n = 1 << logn;
+    const int tps = 1 << log_tps;
+    const int tid = threadIdx.x;
+    const int s = tid >> log_tps;
+    const int t = tid & (tps - 1);
+    const int slot_floats = spb * n;  // one array of one tile
+    float *slots = reinterpret_cast<float *>(smem_raw);
+    const int mstride = tstride<PAD>(tps);
+    float4 *rows_base = reinterpret_cast<float4 *>(slots + NS * 4 * slot_floats);
+    float4 *rows = rows_base + s * mstride;
+    float4 *bnd = rows_base + spb * mstride;
+    int issued[NS], consumed[NS];
+#pragma unroll
+    for (int q = 0; q < NS; ++q) issued[q] = consumed[q] = 0;
+
+    auto issue = [&](int64_t tile, int q) {
+        const int64_t sig0 = tile * spb;
+        const int64_t left = batch - sig0;
+        const int nv = left < spb ? static_cast<int>(left) : spb;
+        const uint32_t bytes = static_cast<uint32_t>(nv) * static_cast<uint32_t>(n) * 4u;
+        float *dst = slots + static_cast<size_t>(q) * 4 * slot_floats;
+        mbar_arrive_expect_tx(&full[q], 4u * bytes);
+        tma_load_1d(dst, ga + sig0 * n, bytes, &full[q]);
+        tma_load_1d(dst + slot_floats, gb + sig0 * n, bytes, &full[q]);
+        tma_load_1d(dst + 2 * slot_floats, gc + sig0 * n, bytes, &full[q]);
+        tma_load_1d(dst + 3 * slot_floats, gd + sig0 * n, bytes, &full[q]);
+        ++issued[q];
+    };
+
+    if (tid == 0) {
+#pragma unroll
+        for (int q = 0; q < NS; ++q) mbar_init(&full[q], 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    if (tid == 0) {
+#pragma unroll
+        for (int q = 0; q < NS; ++q) {
+            const int64_t tile = blockIdx.x + static_cast<int64_t>(q) * gridDim.x;
+            if (tile < ntiles) issue(tile, q);
+        }
+    }
+
+    int k = 0;
+    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++k) {
+        const int q = k % NS;
+        const uint32_t parity = static_cast<uint32_t>(k / NS) & 1u;
+        const int64_t sig0 = tile * spb;
+        const int64_t left = batch - sig0;
+        const int nvalid = left < spb ? static_cast<int>(left) : spb;
+        const bool active = s < nvalid;
+        const bool ok = __syncthreads_and(mbar_wait_bounded(&full[q], parity));
+        if (!ok) {
+            if (tid == 0) {  // drain this block's copies in flight, then leave
+#pragma unroll
+                for (int qq = 0; qq < NS; ++qq)
+                    if (issued[qq] > consumed[qq]) mbar_wait_bounded(&full[qq], static_cast<uint32_t>(consumed[qq]) & 1u);
+            }
+            return;
+        }
+        if (tid == 0) ++consumed[q];
+        float a[P], b[P], c[P], d[P];
+        if (active) {
+            const float *sl = slots + static_cast<size_t>(q) * 4 * slot_floats + s * n + t * P;
+#pragma unroll
+            for (int i = 0; i < P; i += 4) {
+                const float4 va = *reinterpret_cast<const float4 *>(sl + i);
+                const float4 vb = *reinterpret_cast<const float4 *>(sl + slot_floats + i);
+                const float4 vc = *reinterpret_cast<const float4 *>(sl + 2 * slot_floats + i);
+                const float4 vd = *reinterpret_cast<const float4 *>(sl + 3 * slot_floats + i);
+                a[i] = va.x; a[i + 1] = va.y; a[i + 2] = va.z; a[i + 3] = va.w;
+                b[i] = vb.x; b[i + 1] = vb.y; b[i + 2] = vb.z; b[i + 3] = vb.w;
+                c[i] = vc.x; c[i + 1] = vc.y; c[i + 2] = vc.z; c[i + 3] = vc.w;
+                d[i] = vd.x; d[i + 1] = vd.y; d[i + 2] = vd.z; d[i + 3] = vd.w;
+            }
+        } else {
+#pragma unroll
+            for (int i = 0; i < P; ++i) {
+                a[i] = 0.f;
+                b[i] = 1.f;
+                c[i] = 0.f;
+                d[i] = 0.f;
+            }
+        }
+        __syncthreads();  // every run is in registers: refill the slot now
+        const int64_t next = tile + static_cast<int64_t>(NS) * gridDim.x;
+        if (tid == 0 && next < ntiles) {
+            fence_proxy_async();
+            issue(next, q);
+        }
+        if (t == 0) a[0] = 0.f;
+        if (t == tps - 1) c[P - 1] = 0.f;
+        cr_register_solve<P, PAD, SHUFFLE>(a, b, c, d, log_m, log_tps, t, rows, bnd);
+        if (active) store_run<float, P>(x + (sig0 + s) * n + static_cast<int64_t>(t) * P, d);
+    }
+}
+
 // Write the x column (the d components) of the block's rows to global memory.
 template <int PAD>
 __device__ __forceinline__ void tile_store_x(float *x, float4 *rows, int row_stride, int logn, int count) {
@@ -892,6 +1006,14 @@ const void *tri_func_ps(bool refined, int layout, int io, int P) {
         }
     }
     if (layout == 1) return reinterpret_cast<const void *>(&tridiag_compact_kernel<SHUFFLE>);
+    if (layout == 2 && io == 1) {
+        switch (P) {
+            case 4: return reinterpret_cast<const void *>(&tridiag_reg_tma_kernel<4, PAD, SHUFFLE, 1024>);
+            case 8: return reinterpret_cast<const void *>(&tridiag_reg_tma_kernel<8, PAD, SHUFFLE, 512>);
+            case 16: return reinterpret_cast<const void *>(&tridiag_reg_tma_kernel<16, PAD, SHUFFLE, 256>);
+            default: return nullptr;
+        }
+    }
     if (layout == 2) {
         switch (P) {
             case 2: return reinterpret_cast<const void *>(&tridiag_reg_kernel<2, PAD, SHUFFLE, 1024>);
@@ -909,7 +1031,7 @@ const void *tri_func(int pad, int shuffle, bool refined, int layout, int io, int
     if (pad < 0 || pad > 1 || shuffle < 0 || shuffle > 1 || layout < 0 || layout > 6 || io < 0 || io > 1)
         return nullptr;
     if (!refined && layout == 1 && (pad != 1 || io != 0)) return nullptr;
-    if (!refined && layout == 2 && io != 0) return nullptr;
+    if (!refined && layout == 2 && io == 1 && P < 4) return nullptr;
     if (pad) return shuffle ? tri_func_ps<1, 1>(refined, layout, io, P) : tri_func_ps<1, 0>(refined, layout, io, P);
     return shuffle ? tri_func_ps<0, 1>(refined, layout, io, P) : tri_func_ps<0, 0>(refined, layout, io, P);
 }
@@ -922,9 +1044,10 @@ int tridiag_smem_bytes(int pad, int64_t n, int spb, bool refined, int layout, in
     if (!refined && layout == 1) return spb * compact_sys_bytes(ni, levels);
     if (!refined && layout == 2) {
         // middle rows per system + [threads][log2 P] boundary equations
+        // (+ io 1: one slot of the tile's a, b, c, d)
         const int tps = ni / P;
         const int lp = ilog2(P);
-        return spb * 16 * (pad ? tstride<1>(tps) : tps) + spb * tps * lp * 16;
+        return (io == 1 ? 4 * spb * ni * 4 : 0) + spb * 16 * (pad ? tstride<1>(tps) : tps) + spb * tps * lp * 16;
     }
     if (!refined && io == 1) return kTriTmaStages * 16 * spb * ni + spb * 16 * (pad ? tstride<1>(ni) : ni);
     if (!refined) return spb * 16 * (pad ? tstride<1>(ni) : ni);

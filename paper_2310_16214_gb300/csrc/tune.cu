@@ -6,6 +6,7 @@
 #include <algorithm>
 #include <chrono>
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <functional>
 #include <map>
@@ -249,7 +250,7 @@ struct SplitMix {
 std::vector<double> raw_features(const bplg_plan &p) {
     std::vector<double> f = {std::log2(double(p.P)), std::log2(double(p.spb)), double(p.pattern),
                              double(p.smem_pad), std::log2(double(std::max(1, p.cr_switch))), double(p.shuffle)};
-    for (int k = 0; k < 4; ++k) f.push_back(p.smem_layout == k ? 1.0 : 0.0);
+    for (int k = 0; k < 7; ++k) f.push_back(p.smem_layout == k ? 1.0 : 0.0);
     for (int k = 0; k < 3; ++k) f.push_back(p.io == k ? 1.0 : 0.0);
     return f;
 }
@@ -405,6 +406,20 @@ using CostFn = std::function<double(const bplg_plan &)>;
 
 // Search over `plans`; writes the chosen index.  regs/smem (may be empty)
 // feed the analytical method.
+// Stopping window of the learned tuner: the search ends once this many
+// evaluations in a row brought no new best.  Section IV-B uses 5 with
+// GPTune's LCM surrogate; with this single-task GP a 5-evaluation window
+// stopped early on the large tridiagonal spaces (1000-2000 plans), so the
+// default is 8.  BPLG_BO_WINDOW (1..64) overrides it, e.g. 5 for the paper's.
+static int bo_window() {
+    static const int w = [] {
+        const char *e = std::getenv("BPLG_BO_WINDOW");
+        const int v = e ? std::atoi(e) : 0;
+        return (v >= 1 && v <= 64) ? v : 8;
+    }();
+    return w;
+}
+
 int tune_search(const std::vector<bplg_plan> &plans, const std::vector<int> &regs, const std::vector<int> &smem,
                 const bplg_arch &arch, int method, int budget, uint64_t seed, const CostFn &cost, int *chosen,
                 bplg_tune_report *rep) {
@@ -501,7 +516,8 @@ int tune_search(const std::vector<bplg_plan> &plans, const std::vector<int> &reg
             if (far < 0) break;
             next = far;
         }
-        while (r.evaluations < budget && r.evaluations < N && since < 5) {
+        const int window = bo_window();
+        while (r.evaluations < budget && r.evaluations < N && since < window) {
             // training set: log time, invalid points at a high penalty
             std::vector<std::vector<double>> Xs;
             std::vector<double> ys;

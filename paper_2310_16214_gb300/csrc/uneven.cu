@@ -9,11 +9,13 @@
 // Units hold up to spb problems of one size; within a unit the layout is
 // the batched kernels' (one signal per T threads), but every problem has its
 // own input and output pointers, so problems need not be contiguous.
-//   scan     256 threads; P = 4 for n <= 1024, else n / 256 (T <= 256)
-//   FFT      512 threads; radix 16 (mixed-radix first stage), T = n / 16;
-//            n >= 1024 with the compile-time stage schedule
-//   tridiag  512 threads; P = 8 for n <= 4096, else 16; register CR levels,
-//            middle system of T equations by CR/PCR with shuffle PCR
+//   scan     256 threads; P = 16 for n <= 4096, else 32 (T <= 256): enough
+//            bytes in flight per thread to cover the memory latency
+//   FFT      512 threads, two blocks per SM; radix 16 (mixed-radix first
+//            stage), T = n / 16, every size with the compile-time stage
+//            schedule (one non-inlined function per size)
+//   tridiag  1024 threads; P = 8; register CR levels, middle system of T
+//            equations by CR/PCR with shuffle PCR
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -41,12 +43,12 @@ struct UnitDesc {
 
 constexpr int kUnevenScanThreads = 256;
 constexpr int kUnevenFftThreads = 512;
-constexpr int kUnevenTriThreads = 512;
+constexpr int kUnevenTriThreads = 1024;
 constexpr int kUnevenMinLog = 5;
 constexpr int kUnevenMaxLog = 13;
 
-__host__ __device__ inline int uneven_scan_P(int logn) { return logn <= 10 ? 4 : 1 << (logn - 8); }
-__host__ __device__ inline int uneven_tri_P(int logn) { return logn <= 12 ? 8 : 16; }
+__host__ __device__ inline int uneven_scan_P(int logn) { return logn <= 12 ? 16 : 32; }
+__host__ __device__ inline int uneven_tri_P(int logn) { return 8; }
 
 // ------------------------------------------------------------------ scan
 template <typename E, int P>
@@ -126,72 +128,7 @@ __global__ void __launch_bounds__(kUnevenScanThreads)
 }
 
 // ------------------------------------------------------------------- FFT
-template <int DIR>
-__device__ __forceinline__ void fft_unit(const ItemDesc *items, const UnitDesc &U, const float2 *__restrict__ tw,
-                                         float2 *buf) {
-    constexpr int R = 16;
-    constexpr int LR = 4;
-    const int logn = U.logn;
-    const int n = 1 << logn;
-    const int logT = logn - LR;
-    const int T = 1 << logT;
-    const int tid = threadIdx.x;
-    const int s = tid >> logT;
-    const int j = tid & (T - 1);
-    const bool active = s < U.count;
-    const int stride = sig_stride<0, 1>(n);
-    const int sbase = s * stride;
-    float2 v[R];
-    OutMap om{0, 0, 0, 0, 0, j, T};
-    const float2 *in = active ? static_cast<const float2 *>(items[U.first + s].in0) : nullptr;
-#pragma unroll
-    for (int m = 0; m < R; ++m) v[m] = active ? __ldcs(in + j + m * T) : make_float2(0.f, 0.f);
-    const int lr0 = logn % LR;
-    const int nstages = (lr0 ? 1 : 0) + logn / LR;
-    int logNs = 0;
-    for (int st = 0; st < nstages; ++st) {
-        if (st == 0 && lr0 != 0) {
-            if (lr0 == 1) first_stage_mixed<R, 2, DIR>(v);
-            if (lr0 == 2) first_stage_mixed<R, 4, DIR>(v);
-            if (lr0 == 3) first_stage_mixed<R, 8, DIR>(v);
-            om.mixed = 1;
-            om.lr0 = lr0;
-            om.lq = LR - lr0;
-            logNs = lr0;
-        } else {
-            const int Ns = 1 << logNs;
-            const int k = j & (Ns - 1);
-            if (logNs > 0) {
-                const float2 *twp = tw + (Ns << LR);
-#pragma unroll
-                for (int r = 1; r < R; ++r) {
-                    float2 w = __ldg(twp + r * k);
-                    if (DIR > 0) w.y = -w.y;
-                    v[r] = cmul(v[r], w);
-                }
-            }
-            dft_codelet<R, DIR>(v);
-            om.mixed = 0;
-            om.base = ((j >> logNs) << (logNs + LR)) + k;
-            om.shift = logNs;
-            logNs += LR;
-        }
-        if (st == nstages - 1) break;
-        __syncthreads();
-#pragma unroll
-        for (int r = 0; r < R; ++r) buf[sbase + pidx<0, 1>(om(r))] = v[r];
-        __syncthreads();
-#pragma unroll
-        for (int m = 0; m < R; ++m) v[m] = buf[sbase + pidx<0, 1>(j + m * T)];
-    }
-    if (active) {
-        float2 *out = static_cast<float2 *>(items[U.first + s].out);
-#pragma unroll
-        for (int r = 0; r < R; ++r) __stcs(out + om(r), v[r]);
-    }
-}
-
-// n >= 1024: the compile-time stage schedule of the size-specialised
+// One FFT unit: the compile-time stage schedule of the size-specialised
 // batched kernel (constant exchange offsets, unrolled stages).  Not inlined:
 // each size keeps its own register allocation instead of all of them
 // merging into the kernel's.
@@ -216,15 +153,20 @@ template <int DIR>
 __device__ __forceinline__ void fft_unit_any(const ItemDesc *items, const UnitDesc &U, const float2 *__restrict__ tw,
                                              float2 *buf) {
     switch (U.logn) {
+        case 5: fft_unit_fixed<5, DIR>(items, U, tw, buf); break;
+        case 6: fft_unit_fixed<6, DIR>(items, U, tw, buf); break;
+        case 7: fft_unit_fixed<7, DIR>(items, U, tw, buf); break;
+        case 8: fft_unit_fixed<8, DIR>(items, U, tw, buf); break;
+        case 9: fft_unit_fixed<9, DIR>(items, U, tw, buf); break;
         case 10: fft_unit_fixed<10, DIR>(items, U, tw, buf); break;
         case 11: fft_unit_fixed<11, DIR>(items, U, tw, buf); break;
         case 12: fft_unit_fixed<12, DIR>(items, U, tw, buf); break;
         case 13: fft_unit_fixed<13, DIR>(items, U, tw, buf); break;
-        default: fft_unit<DIR>(items, U, tw, buf); break;
+        default: break;  // sizes are checked on the host: 2^5 .. 2^13
     }
 }
 
-__global__ void __launch_bounds__(kUnevenFftThreads)
+__global__ void __launch_bounds__(kUnevenFftThreads, 2)
     uneven_fft_kernel(const ItemDesc *items, const UnitDesc *units, int nunits, int *counter,
                       const float2 *__restrict__ tw) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -286,10 +228,7 @@ __global__ void __launch_bounds__(kUnevenTriThreads)
         __syncthreads();
         if (u >= nunits) break;
         const UnitDesc U = units[u];
-        if (uneven_tri_P(U.logn) == 8)
-            tri_unit<8>(items, U, smem);
-        else
-            tri_unit<16>(items, U, smem);
+        tri_unit<8>(items, U, smem);
         __syncthreads();  // rows and boundary slots are reused by the next unit
     }
 }

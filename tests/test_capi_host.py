@@ -164,13 +164,28 @@ def test_learned_search_is_deterministic():
     assert seen[0] == seen[1]
 
 
-def test_learned_search_stops_after_five_without_progress():
+def test_learned_search_stops_after_the_window_without_progress():
     plans = synthetic_plans()
     chosen, rep = bp.tune_plans_cost(plans, lambda p: 1.0, bp.TUNE_LEARNED, budget=100, seed=1)
-    # a flat surface: the random initial design (5 points, growing with the
-    # square root of the space, at most 24), then 5 evaluations without progress
+    # a flat surface: the initial design (5 points, growing with the square
+    # root of the space, at most 24), then the stopping window (8 by default)
+    # of evaluations without progress
     n0 = max(5, min(math.ceil(0.6 * math.sqrt(len(plans))), 24))
-    assert rep.evaluations == n0 + 5
+    assert rep.evaluations == n0 + 8
+
+
+def test_learned_search_window_of_the_paper():
+    # BPLG_BO_WINDOW=5 restores the 5-evaluation window of Section IV-B
+    import subprocess
+    import sys
+    code = ("import math, sys; sys.path.insert(0, %r); import paper_2310_16214_gb300 as bp; "
+            "from tests.test_capi_host import synthetic_plans; plans = synthetic_plans(); "
+            "c, r = bp.tune_plans_cost(plans, lambda p: 1.0, bp.TUNE_LEARNED, budget=100, seed=1); "
+            "n0 = max(5, min(math.ceil(0.6 * math.sqrt(len(plans))), 24)); print(r.evaluations - n0)" % ROOT)
+    out = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, cwd=ROOT,
+                         env={**os.environ, "BPLG_BO_WINDOW": "5"})
+    assert out.returncode == 0, out.stderr[-2000:]
+    assert out.stdout.strip() == "5"
 
 
 def test_invalid_candidates_are_penalised():
