@@ -76,10 +76,12 @@ def read_peaks():
 # batch, doubled; keyed by row and plan.  A launch whose plan was not captured
 # reports null.
 NCU_TRAFFIC = {
-    # tridiag_refined_reg_kernel<16, 2, 0, 1, 256>: 134.30 MB read + 27.66 MB
-    # written per half-size launch (the rest of x is still in L2 at kernel end)
+    # tridiag_refined_reg_kernel, layout 6: DRAM read + write per half-size
+    # launch, doubled (the rest of x is still in L2 at kernel end)
     ("refined_1024", (("P", 16), ("L", 64), ("spb", 1), ("shuffle", 1), ("pattern", 0), ("smem_layout", 6),
                       ("smem_pad", 0), ("io", 0), ("cr_switch", 32))): 2 * (134301696 + 27660288),
+    ("refined_1024", (("P", 8), ("L", 128), ("spb", 1), ("shuffle", 1), ("pattern", 0), ("smem_layout", 6),
+                      ("smem_pad", 0), ("io", 0), ("cr_switch", 32))): 2 * (134287872 + 28645888),
 }
 
 # FP64 issue rate of one SM: 2 double-precision fused multiply-adds per clock
