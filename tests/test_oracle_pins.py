@@ -121,6 +121,29 @@ def test_fft_invariants():
     assert np.allclose(R[:, 1:], np.conj(R[:, :0:-1]), atol=1e-11)
 
 
+@pytest.mark.parametrize("n", [1 << 15, 1 << 18, 1 << 20])
+def test_fft_large_vs_numpy(n):
+    # the sizes of the two-pass large-transform path
+    x = si.fft_c64(2, n, stream=31).astype(np.complex128)
+    for d in (-1, 1):
+        X = oracle.fft(x, d)
+        ref = np.fft.fft(x, axis=-1) if d < 0 else n * np.fft.ifft(x, axis=-1)
+        assert np.linalg.norm(X - ref) / np.linalg.norm(ref) < 1e-13
+
+
+def test_fft_large_closed_forms():
+    n = 1 << 20
+    k = np.arange(n)
+    m = 12345
+    dm = np.zeros((1, n), np.complex128)
+    dm[0, m] = 1
+    assert np.allclose(oracle.fft(dm, -1)[0], np.exp(-2j * np.pi * m * k / n), atol=1e-11)
+    k0 = 777
+    tone = np.exp(2j * np.pi * k0 * k / n)[None, :]
+    X = oracle.fft(tone, -1)[0]
+    assert abs(X[k0] - n) < 1e-6 * n and np.max(np.abs(np.delete(X, k0))) < 1e-6 * n
+
+
 def test_fft_rejects_non_pow2():
     with pytest.raises(ValueError):
         oracle.fft(np.zeros((1, 12), np.complex128))
