@@ -100,6 +100,18 @@ typedef enum { BPLG_TC_BF16 = 0, BPLG_TC_F16 = 1 } bplg_tc_precision;
  *           per block, 1 persistent blocks fed by bulk asynchronous copies.
  *   cr_switch tridiag: system size m at which cyclic reduction hands over to
  *           parallel cyclic reduction (1 = pure CR, n = pure PCR).
+ *   n1_log  FFT with n > 16384, computed in two kernels (the multi-kernel
+ *           transform of Section V-C for signals that do not fit one
+ *           block): n = N1 N2 with N1 = 2^n1_log.  The first kernel runs the
+ *           N1-point transforms of the columns of the N1 x N2 row-major
+ *           signal, spb adjacent columns per block, and multiplies by
+ *           exp(dir 2 pi i k1 n2 / n); the second runs the N2-point
+ *           transforms of the rows, row_spb rows per block, and writes the
+ *           result in natural order.  Both use radix 16 (P = radix = 16,
+ *           padded interleaved exchanges, io 0) and L = spb * N1 / 16.
+ *           0 for every other plan.
+ *   row_spb FFT with n > 16384: rows per block of the second kernel.
+ *   reserved 0.
  */
 typedef struct {
     int32_t op;
@@ -115,7 +127,9 @@ typedef struct {
     int32_t smem_pad;
     int32_t io;
     int32_t cr_switch;
-    int32_t reserved[3];
+    int32_t n1_log;
+    int32_t row_spb;
+    int32_t reserved;
 } bplg_plan;
 
 /* -------------------------------------------------------- compute calls */
@@ -134,7 +148,11 @@ int bplg_scan_batched(int32_t dtype, const void *in, void *out, int64_t n, int64
  * with dir = -1 (forward) or +1 (inverse, unnormalised), natural order.
  *   in,out device, [batch][n] complex64 as interleaved (re, im) float pairs;
  *          in == out is allowed.
- *   n      power of two, 2 <= n <= 16384; batch >= 1.
+ *   n      power of two, 2 <= n <= 2^24; batch >= 1.  Above 16384 points the
+ *          transform runs as two kernels (see n1_log in the plan) through a
+ *          scratch buffer of n * batch complex values that the library
+ *          allocates on first use per device and grows when needed (a growth
+ *          synchronises the device); in may equal out.
  * Twiddles W_M^k are generated once per device in float64 and rounded to
  * float32.  Errors: INVALID_ARG, UNSUPPORTED_SIZE, INVALID_PLAN, CUDA. */
 int bplg_fft_batched(const void *in, void *out, int64_t n, int64_t batch, int32_t dir,

@@ -53,7 +53,7 @@ class BplgError(RuntimeError):
 class Plan(ctypes.Structure):
     _fields_ = [(name, ctypes.c_int32) for name in (
         "op", "n", "P", "L", "spb", "S", "radix", "shuffle", "pattern", "smem_layout", "smem_pad",
-        "io", "cr_switch")] + [("reserved", ctypes.c_int32 * 3)]
+        "io", "cr_switch", "n1_log", "row_spb", "reserved")]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}
@@ -174,6 +174,16 @@ def _plan_ref(plan: Optional[Plan]):
     return ctypes.byref(plan) if plan is not None else None
 
 
+def _need(name: str, t, nbytes: int) -> None:
+    """A tensor argument must hold at least nbytes (the C ABI takes bare
+    pointers and cannot check); raw integer pointers are the caller's."""
+    if t is None or isinstance(t, int) or nbytes <= 0:
+        return
+    have = t.numel() * t.element_size()
+    if have < nbytes:
+        raise ValueError("%s holds %d bytes, the call needs %d" % (name, have, nbytes))
+
+
 # ------------------------------------------------------------- compute calls
 
 def scan_batched(inp, out, n: int, batch: int, dtype: Optional[int] = None, plan: Optional[Plan] = None,
@@ -182,17 +192,23 @@ def scan_batched(inp, out, n: int, batch: int, dtype: Optional[int] = None, plan
     if dtype is None:
         import torch
         dtype = I32 if inp.dtype == torch.int32 else F32
+    _need("in", inp, 4 * n * batch)
+    _need("out", out, 4 * n * batch)
     _check(lib.bplg_scan_batched(dtype, _ptr(inp), _ptr(out), n, batch, _plan_ref(plan), _stream(stream)))
 
 
 def fft_batched(inp, out, n: int, batch: int, direction: int = -1, plan: Optional[Plan] = None, stream=None) -> None:
     """Complex Stockham FFT of [batch][n] complex64 (see bplg_fft_batched)."""
+    _need("in", inp, 8 * n * batch)
+    _need("out", out, 8 * n * batch)
     _check(lib.bplg_fft_batched(_ptr(inp), _ptr(out), n, batch, direction, _plan_ref(plan), _stream(stream)))
 
 
 def fft_tc_batched(inp, out, n: int, batch: int, direction: int = -1, precision: int = TC_BF16,
                    plan: Optional[Plan] = None, stream=None) -> None:
     """FFT with tensor-core radix-16 stages, split hi/lo operands (see bplg_fft_tc_batched)."""
+    _need("in", inp, 8 * n * batch)
+    _need("out", out, 8 * n * batch)
     _check(lib.bplg_fft_tc_batched(_ptr(inp), _ptr(out), n, batch, direction, precision, _plan_ref(plan),
                                    _stream(stream)))
 
@@ -200,12 +216,16 @@ def fft_tc_batched(inp, out, n: int, batch: int, direction: int = -1, precision:
 def fft_batched_noalloc(inp, out, n: int, batch: int, direction: int = -1, plan: Optional[Plan] = None,
                         stream=None) -> None:
     """The FFT without any device allocation, n <= 4096 (see bplg_fft_batched_noalloc)."""
+    _need("in", inp, 8 * n * batch)
+    _need("out", out, 8 * n * batch)
     _check(lib.bplg_fft_batched_noalloc(_ptr(inp), _ptr(out), n, batch, direction, _plan_ref(plan),
                                         _stream(stream)))
 
 
 def tridiag_batched(a, b, c, d, x, n: int, batch: int, plan: Optional[Plan] = None, stream=None) -> None:
     """CR/PCR tridiagonal solve of [batch][n] float32 systems (see bplg_tridiag_batched)."""
+    for name, t in (("a", a), ("b", b), ("c", c), ("d", d), ("x", x)):
+        _need(name, t, 4 * n * batch)
     _check(lib.bplg_tridiag_batched(_ptr(a), _ptr(b), _ptr(c), _ptr(d), _ptr(x), n, batch, _plan_ref(plan),
                                     _stream(stream)))
 
@@ -213,6 +233,10 @@ def tridiag_batched(a, b, c, d, x, n: int, batch: int, plan: Optional[Plan] = No
 def tridiag_refined(a, b, c, d, x, n: int, batch: int, max_iter: int = 10, tol: float = 1e-14, iters=None,
                     plan: Optional[Plan] = None, stream=None) -> None:
     """Float64-residual refined solve; x is float64 (see bplg_tridiag_refined)."""
+    for name, t in (("a", a), ("b", b), ("c", c), ("d", d)):
+        _need(name, t, 4 * n * batch)
+    _need("x", x, 8 * n * batch)
+    _need("iters", iters, 4 * batch)
     _check(lib.bplg_tridiag_refined(_ptr(a), _ptr(b), _ptr(c), _ptr(d), _ptr(x), n, batch, max_iter, tol,
                                     _ptr(iters), _plan_ref(plan), _stream(stream)))
 

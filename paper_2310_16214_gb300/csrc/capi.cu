@@ -102,7 +102,7 @@ int bplg_fft_batched(const void *in, void *out, int64_t n, int64_t batch, int32_
     if (!in || !out) return set_error(BPLG_ERR_INVALID_ARG, "fft: null buffer");
     if (n < 1 || batch < 1) return set_error(BPLG_ERR_INVALID_ARG, "fft: n and batch must be >= 1");
     if (dir != -1 && dir != 1) return set_error(BPLG_ERR_INVALID_ARG, "fft: dir must be -1 or +1");
-    if (!size_ok(BPLG_OP_FFT, n, 2)) return set_error(BPLG_ERR_UNSUPPORTED_SIZE, "fft: n must be a power of two in [2, 16384]");
+    if (!size_ok(BPLG_OP_FFT, n, 2)) return set_error(BPLG_ERR_UNSUPPORTED_SIZE, "fft: n must be a power of two in [2, 2^24]");
     if (!aligned16(in) || !aligned16(out)) return set_error(BPLG_ERR_INVALID_ARG, "fft: buffers must be 16-byte aligned");
     bplg_plan p;
     int rc = resolve_plan(BPLG_OP_FFT, BPLG_F32, n, batch, plan, &p);

@@ -707,6 +707,7 @@ int twiddles_for_current_device(const void **tw) {
 }
 
 bool fft_launch_info(const bplg_plan &p, int64_t n, int64_t batch, int dir, Launch *out) {
+    if (n > (int64_t(1) << kFftMaxLog)) return fft_large_launch_info(p, n, batch, dir, 0, out);
     std::string why;
     if (!plan_structurally_valid(p, BPLG_F32, n, &why)) return false;
     const void *f = fft_func(p.radix, dir, p.smem_layout, p.smem_pad, p.io, p.L, ilog2(n));
@@ -720,6 +721,7 @@ bool fft_launch_info(const bplg_plan &p, int64_t n, int64_t batch, int dir, Laun
 
 int fft_launch(const bplg_plan &p, const void *in, void *out, int64_t n, int64_t batch, int dir,
                cudaStream_t s) {
+    if (n > (int64_t(1) << kFftMaxLog)) return fft_large_launch(p, in, out, n, batch, dir, s);
     Launch li;
     if (!fft_launch_info(p, n, batch, dir, &li)) return set_error(BPLG_ERR_INVALID_PLAN, "fft: plan has no kernel");
     const void *tw = nullptr;

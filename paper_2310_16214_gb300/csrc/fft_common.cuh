@@ -185,9 +185,12 @@ struct StageOut {
     }
 };
 
-template <int R, int LOGN, int DIR, int LAYOUT, int ST>
-__device__ __forceinline__ void fft_fixed_stages(float2 (&v)[R], float2 *buf2, float *buf1, int j,
-                                                 const float2 *__restrict__ tw, float2 *gout, bool active) {
+// The last stage hands each output, with its natural-order position, to
+// store(position, value); with SYNC_LAST the block synchronises first (for a
+// store into the exchange buffer that other threads may still be reading).
+template <int R, int LOGN, int DIR, int LAYOUT, int ST, bool SYNC_LAST = false, class Store>
+__device__ __forceinline__ void fft_fixed_stages_st(float2 (&v)[R], float2 *buf2, float *buf1, int j,
+                                                    const float2 *__restrict__ tw, Store &store) {
     using S = FftShape<R, LOGN>;
     using O = StageOut<R, LOGN, ST>;
     constexpr int G = LAYOUT == 0 ? 16 : 32;
@@ -209,10 +212,9 @@ __device__ __forceinline__ void fft_fixed_stages(float2 (&v)[R], float2 *buf2, f
     }
     const int ob = O::base(j);
     if constexpr (ST == S::NST - 1) {
-        if (active) {
+        if constexpr (SYNC_LAST) __syncthreads();
 #pragma unroll
-            for (int r = 0; r < R; ++r) __stcs(gout + ob + O::off(r), v[r]);
-        }
+        for (int r = 0; r < R; ++r) store(ob + O::off(r), v[r]);
     } else {
         const int pb = pad_g<G>(ob);
         const int pj = pad_g<G>(j);
@@ -237,8 +239,19 @@ __device__ __forceinline__ void fft_fixed_stages(float2 (&v)[R], float2 *buf2, f
 #pragma unroll
             for (int m = 0; m < R; ++m) v[m].y = buf1[pj + m * S::T + (m * S::T) / G];
         }
-        fft_fixed_stages<R, LOGN, DIR, LAYOUT, ST + 1>(v, buf2, buf1, j, tw, gout, active);
+        fft_fixed_stages_st<R, LOGN, DIR, LAYOUT, ST + 1, SYNC_LAST>(v, buf2, buf1, j, tw, store);
     }
+}
+
+// The stage schedule with the last stage stored straight to global memory
+// (natural order, streaming stores) when `active`.
+template <int R, int LOGN, int DIR, int LAYOUT, int ST>
+__device__ __forceinline__ void fft_fixed_stages(float2 (&v)[R], float2 *buf2, float *buf1, int j,
+                                                 const float2 *__restrict__ tw, float2 *gout, bool active) {
+    auto store = [&](int pos, float2 val) {
+        if (active) __stcs(gout + pos, val);
+    };
+    fft_fixed_stages_st<R, LOGN, DIR, LAYOUT, ST>(v, buf2, buf1, j, tw, store);
 }
 
 }  // namespace bplg

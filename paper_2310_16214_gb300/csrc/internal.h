@@ -36,7 +36,8 @@ struct Launch {
 
 // Largest sizes each family supports.
 constexpr int kScanMaxLog = 15;
-constexpr int kFftMaxLog = 14;
+constexpr int kFftMaxLog = 14;       // one block per signal
+constexpr int kFftLargeMaxLog = 24;  // two-kernel transforms beyond that
 constexpr int kTridiagMaxLog = 13;
 constexpr int kRefinedMaxLog = 12;
 
@@ -51,6 +52,15 @@ int fft_launch(const bplg_plan &p, const void *in, void *out, int64_t n, int64_t
 
 int fft_tc_launch(const bplg_plan &p, const void *in, void *out, int64_t n, int64_t batch, int dir, int prec,
                   cudaStream_t s);
+
+// two-kernel FFT for n > 2^kFftMaxLog (fft_large.cu); pass 0 = columns, 1 = rows
+bool fft_large_plan_valid(const bplg_plan &p, int64_t n, std::string *why);
+void fft_large_finalize(bplg_plan *p, int64_t n);
+std::vector<bplg_plan> fft_large_enumerate(int64_t n);
+int fft_large_smem_bytes(const bplg_plan &p, int64_t n, int pass);
+bool fft_large_launch_info(const bplg_plan &p, int64_t n, int64_t batch, int dir, int pass, Launch *out);
+int fft_large_launch(const bplg_plan &p, const void *in, void *out, int64_t n, int64_t batch, int dir,
+                     cudaStream_t s);
 
 bool tridiag_launch_info(const bplg_plan &p, int64_t n, int64_t batch, bool refined, Launch *out);
 int tridiag_launch(const bplg_plan &p, const float *a, const float *b, const float *c,

@@ -4,6 +4,7 @@
 // and the per-device dynamic shared-memory opt-in.
 #include <cstdio>
 #include <cstdlib>
+#include <algorithm>
 #include <cstring>
 #include <fstream>
 #include <map>
@@ -64,7 +65,7 @@ static bool fail(std::string *why, const char *msg) {
 int max_log_for(int op) {
     switch (op) {
         case BPLG_OP_SCAN: return kScanMaxLog;
-        case BPLG_OP_FFT: return kFftMaxLog;
+        case BPLG_OP_FFT: return kFftLargeMaxLog;
         case BPLG_OP_TRIDIAG: return kTridiagMaxLog;
         case BPLG_OP_TRIDIAG_REFINED: return kRefinedMaxLog;
         case BPLG_OP_FFT_TC: return kFftMaxLog;
@@ -77,6 +78,9 @@ bool plan_structurally_valid(const bplg_plan &p, int dtype, int64_t n, std::stri
     if (ml < 0) return fail(why, "unknown op");
     if (!is_pow2(n) || n > (int64_t(1) << ml)) return fail(why, "n is not a supported power of two");
     if (p.n != 0 && p.n != n) return fail(why, "plan was made for another n");
+    if (p.op == BPLG_OP_FFT && n > (int64_t(1) << kFftMaxLog)) return fft_large_plan_valid(p, n, why);
+    if (p.n1_log != 0 || p.row_spb != 0 || p.reserved != 0)
+        return fail(why, "n1_log, row_spb and reserved are 0 except for FFTs above 16384 points");
     if (!is_pow2(p.P) || p.P > 32 || p.P > n) return fail(why, "P must be a power of two <= min(32, n)");
     if (p.spb < 1) return fail(why, "spb must be >= 1");
     const int64_t tps = n / p.P;
@@ -140,6 +144,8 @@ bool plan_structurally_valid(const bplg_plan &p, int dtype, int64_t n, std::stri
 
 int plan_smem_bytes(const bplg_plan &p, int dtype, int64_t n) {
     (void)dtype;
+    if (p.op == BPLG_OP_FFT && n > (int64_t(1) << kFftMaxLog))
+        return std::max(fft_large_smem_bytes(p, n, 0), fft_large_smem_bytes(p, n, 1));
     switch (p.op) {
         case BPLG_OP_SCAN: return 0;
         case BPLG_OP_FFT: return fft_smem_bytes(p.radix, p.smem_layout, p.smem_pad, p.io, n, p.spb);
@@ -153,6 +159,10 @@ int plan_smem_bytes(const bplg_plan &p, int dtype, int64_t n) {
 }
 
 void plan_finalize(bplg_plan *p, int dtype, int64_t n) {
+    if (p->op == BPLG_OP_FFT && n > (int64_t(1) << kFftMaxLog)) {
+        fft_large_finalize(p, n);
+        return;
+    }
     p->n = static_cast<int32_t>(n);
     const int64_t tps = p->P > 0 ? n / p->P : 0;
     p->L = static_cast<int32_t>(p->spb * tps);
@@ -186,12 +196,13 @@ void plan_finalize(bplg_plan *p, int dtype, int64_t n) {
         default:
             break;
     }
-    std::memset(p->reserved, 0, sizeof(p->reserved));
+    p->n1_log = p->row_spb = p->reserved = 0;
 }
 
 std::vector<bplg_plan> enumerate_structural(int op, int dtype, int64_t n) {
     std::vector<bplg_plan> out;
     if (max_log_for(op) < 0 || !is_pow2(n) || n > (int64_t(1) << max_log_for(op))) return out;
+    if (op == BPLG_OP_FFT && n > (int64_t(1) << kFftMaxLog)) return fft_large_enumerate(n);
     auto push = [&](bplg_plan p) {
         plan_finalize(&p, dtype, n);
         if (plan_structurally_valid(p, dtype, n, nullptr)) out.push_back(p);
@@ -318,13 +329,17 @@ int persistent_grid(const void *func, int threads, int smem, int64_t items, int6
 bool launch_info_for(const bplg_plan &p, int dtype, int64_t n, Launch *li) {
     switch (p.op) {
         case BPLG_OP_SCAN: return scan_launch_info(p, dtype, n, 1, li);
-        case BPLG_OP_FFT: return fft_launch_info(p, n, 1, -1, li);
+        case BPLG_OP_FFT:
+            if (n > (int64_t(1) << kFftMaxLog)) return fft_large_launch_info(p, n, 1, -1, 0, li);
+            return fft_launch_info(p, n, 1, -1, li);
         case BPLG_OP_TRIDIAG: return tridiag_launch_info(p, n, 1, false, li);
         case BPLG_OP_TRIDIAG_REFINED: return tridiag_launch_info(p, n, 1, true, li);
         case BPLG_OP_FFT_TC: return fft_tc_launch_info(p, n, 1, BPLG_TC_BF16, -1, li);
         default: return false;
     }
 }
+
+static int check_launch_on_device(const Launch &li, std::string *why);
 
 int check_plan_on_device(const bplg_plan &p, int dtype, int64_t n, std::string *why) {
     if (!plan_structurally_valid(p, dtype, n, why)) return BPLG_ERR_INVALID_PLAN;
@@ -333,6 +348,19 @@ int check_plan_on_device(const bplg_plan &p, int dtype, int64_t n, std::string *
         if (why) *why = "no kernel for this knob tuple";
         return BPLG_ERR_INVALID_PLAN;
     }
+    if (p.op == BPLG_OP_FFT && n > (int64_t(1) << kFftMaxLog)) {  // the row kernel too
+        Launch l2;
+        if (!fft_large_launch_info(p, n, 1, -1, 1, &l2)) {
+            if (why) *why = "no row kernel for this knob tuple";
+            return BPLG_ERR_INVALID_PLAN;
+        }
+        const int rc = check_launch_on_device(l2, why);
+        if (rc != BPLG_OK) return rc;
+    }
+    return check_launch_on_device(li, why);
+}
+
+static int check_launch_on_device(const Launch &li, std::string *why) {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return cuda_error(e, "cudaGetDevice");
@@ -383,6 +411,11 @@ void load_cache_locked() {
         if (!(ss >> op >> dtype >> n >> bc >> p.op >> p.n >> p.P >> p.L >> p.spb >> p.S >> p.radix >> p.shuffle >>
               p.pattern >> p.smem_layout >> p.smem_pad >> p.io >> p.cr_switch))
             continue;
+        int n1 = 0, rs = 0;
+        if (ss >> n1 >> rs) {
+            p.n1_log = n1;
+            p.row_spb = rs;
+        }
         if (plan_structurally_valid(p, dtype, n, nullptr)) g_cache[std::make_tuple(op, dtype, n, bc)] = p;
     }
 }
@@ -391,13 +424,13 @@ void save_cache_locked() {
     const char *f = cache_file();
     if (!f) return;
     std::ofstream out(f, std::ios::trunc);
-    out << "# op dtype n batch_log2 | op n P L spb S radix shuffle pattern layout pad io cr_switch\n";
+    out << "# op dtype n batch_log2 | op n P L spb S radix shuffle pattern layout pad io cr_switch n1_log row_spb\n";
     for (const auto &kv : g_cache) {
         const bplg_plan &p = kv.second;
         out << std::get<0>(kv.first) << ' ' << std::get<1>(kv.first) << ' ' << std::get<2>(kv.first) << ' '
             << std::get<3>(kv.first) << ' ' << p.op << ' ' << p.n << ' ' << p.P << ' ' << p.L << ' ' << p.spb << ' '
             << p.S << ' ' << p.radix << ' ' << p.shuffle << ' ' << p.pattern << ' ' << p.smem_layout << ' '
-            << p.smem_pad << ' ' << p.io << ' ' << p.cr_switch << '\n';
+            << p.smem_pad << ' ' << p.io << ' ' << p.cr_switch << ' ' << p.n1_log << ' ' << p.row_spb << '\n';
     }
 }
 }  // namespace

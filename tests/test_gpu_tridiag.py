@@ -128,11 +128,11 @@ def test_refined_zero_iterations_is_the_float32_solve(bp):
 
 
 def test_argument_errors(bp):
-    v = torch.zeros(4096, dtype=torch.float32, device="cuda")
+    v = torch.zeros(8192, dtype=torch.float32, device="cuda")
     with pytest.raises(bp.BplgError) as e:
         bp.tridiag_batched(v, v, v, v, v, 100, 1)
     assert e.value.code == bp.ERR_UNSUPPORTED_SIZE
-    x64 = torch.zeros(4096, dtype=torch.float64, device="cuda")
+    x64 = torch.zeros(8192, dtype=torch.float64, device="cuda")
     with pytest.raises(bp.BplgError) as e:
         bp.tridiag_refined(v, v, v, v, v, 64, 1)  # x aliases the inputs
     assert e.value.code == bp.ERR_INVALID_ARG
