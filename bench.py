@@ -871,6 +871,66 @@ def uneven_report(args):
     return row
 
 
+def largefft_report(args):
+    """FFTs above 16384 points (two kernels), N in {2^16, 2^18, 2^20, 2^22},
+    2^24 / N signals: the analytical, learned and exhaustive plans over the
+    joint knob space (split N1, columns per block, rows per block), each
+    re-timed, Phi for both tuners, and cuFFT on the same workload.  The
+    algorithmic bytes are 16 per element, though the two passes move 32."""
+    import ctypes
+    import torch
+    torch.cuda.set_device(0)
+    import paper_2310_16214_gb300 as bp
+    peak, _ = read_peaks()
+    st = torch.cuda.current_stream()
+    lib = ctypes.CDLL(os.path.join(ROOT, "paper_2310_16214_gb300", "_lib", "libbplg_extref.so"))
+    lib.extref_fft_c2c.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64, ctypes.c_int,
+                                   ctypes.c_void_p]
+
+    def timeit(fn):
+        for _ in range(3):
+            fn()
+        evs = []
+        for _ in range(args.reps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(st)
+            fn()
+            e1.record(st)
+            evs.append((e0, e1))
+        torch.cuda.synchronize()
+        return statistics.median(a.elapsed_time(b) for a, b in evs)
+
+    rows, e_an, e_le = [], [], []
+    for logn in (16, 18, 20, 22):
+        n = 1 << logn
+        batch = (1 << 24) // n
+        zin = torch.rand(2 * n * batch, device="cuda") * 2 - 1
+        zout = torch.empty_like(zin)
+        pa, _ = bp.tune_plan(bp.OP_FFT, bp.F32, n, batch, bp.TUNE_ANALYTIC)
+        pl, rl = bp.tune_plan(bp.OP_FFT, bp.F32, n, batch, bp.TUNE_LEARNED, budget=args.bo_budget, seed=args.seed)
+        pe, re_ = bp.tune_plan(bp.OP_FFT, bp.F32, n, batch, bp.TUNE_EXHAUSTIVE)
+        t = {k: timeit(lambda p=p: bp.fft_batched(zin, zout, n, batch, -1, plan=p))
+             for k, p in (("analytic", pa), ("learned", pl), ("exhaustive", pe))}
+        best = min(t.values())
+        tc = timeit(lambda: lib.extref_fft_c2c(ctypes.c_void_p(zin.data_ptr()), ctypes.c_void_p(zout.data_ptr()), n,
+                                               batch, -1, ctypes.c_void_p(st.cuda_stream)))
+        e_an.append(best / t["analytic"])
+        e_le.append(best / t["learned"])
+        row = {"n": n, "batch": batch, "space": re_.space_size, "bo_evaluations": rl.evaluations,
+               "ms": {k: round(v, 5) for k, v in t.items()},
+               "gelem_s": round(n * batch / (best * 1e-3) / 1e9, 1),
+               "hbm_frac_algorithmic": round(16 * n * batch / (best * 1e-3) / 1e9 / peak, 4),
+               "hbm_frac_two_pass": round(32 * n * batch / (best * 1e-3) / 1e9 / peak, 4),
+               "cufft_ms": round(tc, 5), "ours_speedup_vs_cufft": round(tc / best, 3),
+               "plans": {k: {"n1_log": p.n1_log, "spb": p.spb, "row_spb": p.row_spb}
+                         for k, p in (("analytic", pa), ("learned", pl), ("exhaustive", pe))}}
+        rows.append(row)
+        print(json.dumps(row), flush=True)
+    phi = lambda es: round(len(es) / sum(1.0 / e for e in es), 4)
+    print(json.dumps({"largefft_report": {"phi_analytic": phi(e_an), "phi_learned": phi(e_le)}}), flush=True)
+    return rows
+
+
 def precision_report(args):
     """Precision configuration: FFT N in {2^10, 2^12, 2^14}, batch 2^26/N,
     tensor-core radix-16 stages with BF16 and FP16 split operands against
@@ -938,6 +998,8 @@ def main():
     ap.add_argument("--tune-report", action="store_true", help="tuned vs exhaustive Phi report instead of the bench")
     ap.add_argument("--precision-report", action="store_true",
                     help="tensor-core (BF16/FP16 split) vs float32 FFT: error and time per N")
+    ap.add_argument("--largefft-report", action="store_true",
+                    help="FFTs above 16384 points: tuners vs exhaustive (Phi) and cuFFT")
     ap.add_argument("--uneven-report", action="store_true",
                     help="the uneven batch's graph launch against one tuned batched launch per size class")
     ap.add_argument("--ops", default="", help="comma-separated ops for --tune-report")
@@ -956,6 +1018,8 @@ def main():
         precision_report(args)
     elif args.uneven_report:
         uneven_report(args)
+    elif args.largefft_report:
+        largefft_report(args)
     elif args.impl == "reference":
         run_reference(args)
     else:

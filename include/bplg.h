@@ -110,7 +110,9 @@ typedef enum { BPLG_TC_BF16 = 0, BPLG_TC_F16 = 1 } bplg_tc_precision;
  *           result in natural order.  Both use radix 16 (P = radix = 16,
  *           padded interleaved exchanges, io 0) and L = spb * N1 / 16.
  *           0 for every other plan.
- *   row_spb FFT with n > 16384: rows per block of the second kernel.
+ *   row_spb FFT with n > 16384: rows per block of the second kernel
+ *           (spb and row_spb are powers of two up to 64, with 32 to 1024
+ *           threads and at most 227 KB of shared memory per block).
  *   reserved 0.
  */
 typedef struct {

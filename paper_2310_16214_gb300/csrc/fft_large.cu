@@ -242,7 +242,9 @@ bool fft_large_plan_valid(const bplg_plan &p, int64_t n, std::string *why) {
     if (p.P != 16 || p.radix != 16) return fail("FFT above 16384 points: radix and P are 16");
     if (l1 < kLargeMinPassLog || l1 > kLargeMaxPassLog || l2 < kLargeMinPassLog || l2 > kLargeMaxPassLog)
         return fail("FFT above 16384 points: both N1 = 2^n1_log and n / N1 between 64 and 16384");
-    if (!pow2_in(p.spb, 1, 16) || !pow2_in(p.row_spb, 1, 16)) return fail("FFT above 16384 points: spb, row_spb in 1..16");
+    if (!pow2_in(p.spb, 1, 64) || !pow2_in(p.row_spb, 1, 64)) return fail("FFT above 16384 points: spb, row_spb in 1..64");
+    if (fft_large_smem_bytes(p, n, 0) > 227 * 1024 || fft_large_smem_bytes(p, n, 1) > 227 * 1024)
+        return fail("FFT above 16384 points: shared memory above 227 KB per block");
     const int64_t t1 = int64_t(p.spb) << (l1 - 4), t2 = int64_t(p.row_spb) << (l2 - 4);
     if (t1 < 32 || t1 > 1024 || t2 < 32 || t2 > 1024)
         return fail("FFT above 16384 points: 32 to 1024 threads per block in both kernels");
@@ -266,8 +268,8 @@ std::vector<bplg_plan> fft_large_enumerate(int64_t n) {
     std::vector<bplg_plan> out;
     const int logn = ilog2(n);
     for (int l1 = kLargeMinPassLog; l1 <= kLargeMaxPassLog; ++l1) {
-        for (int c = 1; c <= 16; c *= 2) {
-            for (int r = 1; r <= 16; r *= 2) {
+        for (int c = 1; c <= 64; c *= 2) {
+            for (int r = 1; r <= 64; r *= 2) {
                 bplg_plan p;
                 std::memset(&p, 0, sizeof(p));
                 p.op = BPLG_OP_FFT;
