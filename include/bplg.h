@@ -30,9 +30,11 @@
  *   - Streams: `stream` is a cudaStream_t passed as void* (NULL = the legacy
  *     default stream).  Compute entry points are asynchronous on it; argument
  *     errors are reported before anything is enqueued.
- *   - Plans: a NULL plan means "the plan bplg_query_plan returns".  A non-NULL
- *     plan is validated against the size and the device; an unusable plan
- *     returns BPLG_ERR_INVALID_PLAN without launching.
+ *   - Plans: a NULL plan means "the plan bplg_query_plan returns" (with
+ *     online tuning on, a candidate of the online search instead; see
+ *     bplg_set_online_tuning).  A non-NULL plan is validated against the size
+ *     and the device; an unusable plan returns BPLG_ERR_INVALID_PLAN without
+ *     launching.
  */
 #ifndef BPLG_H
 #define BPLG_H
@@ -376,6 +378,29 @@ int bplg_tune_plans_cost(const bplg_plan *plans, int32_t count, const int32_t *r
  * analytical guideline on the current device.
  * Errors: INVALID_ARG, UNSUPPORTED_SIZE, CUDA, NO_DEVICE. */
 int bplg_query_plan(int32_t op, int32_t dtype, int64_t n, int64_t batch, bplg_plan *out);
+
+/* Online tuning: the learned search of Section IV-B spread over the
+ * library's own calls (the paper tunes once, up front; this amortises the
+ * evaluations over repeated calls).  With it on, a compute call that passes
+ * no plan and finds no tuned plan in the cache runs the next candidate of a
+ * search kept per (device, op, dtype, n, batch class), timed by two CUDA
+ * events recorded around its launch on the caller's stream.  A later call
+ * of the same shape reads that time without waiting; while a measurement is
+ * still in flight, or after the search has finished, calls run the best plan
+ * seen so far.  When the search stops (its stopping window or `budget`
+ * evaluations), the best plan enters the plan cache, where bplg_query_plan
+ * and every later call find it.  Results are exact throughout (every
+ * candidate is a valid plan); only speed varies while the search runs.
+ *   enable  1 on, 0 off (the searches in progress are kept).
+ *   budget  evaluations per shape (0 = 40); seed: the search's seed.
+ * Errors: INVALID_ARG. */
+int bplg_set_online_tuning(int32_t enable, int32_t budget, uint64_t seed);
+
+/* Progress of the online search for one shape: evaluations so far, whether
+ * it has finished, and its best plan so far (zeroed when none).
+ * Errors: INVALID_ARG, CUDA. */
+int bplg_online_status(int32_t op, int32_t dtype, int64_t n, int64_t batch, int32_t *evaluations,
+                       int32_t *finished, bplg_plan *best);
 
 /* Median time in milliseconds of `reps` launches of `plan` (after two
  * warm-up launches) on library-owned buffers of shape (dtype, n, batch),

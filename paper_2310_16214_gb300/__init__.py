@@ -40,7 +40,7 @@ EXPORTED = [
     "bplg_arch_query", "bplg_arch_preset", "bplg_occupancy", "bplg_guideline_select", "bplg_phi",
     "bplg_enumerate_plans", "bplg_plan_resources", "bplg_tune_plan", "bplg_tune_plans_cost",
     "bplg_query_plan", "bplg_time_plan", "bplg_check_plan", "bplg_device_status", "bplg_last_error",
-    "bplg_version",
+    "bplg_version", "bplg_set_online_tuning", "bplg_online_status",
 ]
 
 
@@ -123,6 +123,8 @@ def _load():
                                   I32_, ctypes.c_uint64, COST_FN, P, ctypes.POINTER(I32_),
                                   ctypes.POINTER(TuneReport)], ctypes.c_int),
         "bplg_query_plan": ([I32_, I32_, I64, I64, PP], ctypes.c_int),
+        "bplg_set_online_tuning": ([I32_, I32_, ctypes.c_uint64], ctypes.c_int),
+        "bplg_online_status": ([I32_, I32_, I64, I64, ctypes.POINTER(I32_), ctypes.POINTER(I32_), PP], ctypes.c_int),
         "bplg_time_plan": ([PP, I32_, I64, I64, I32_, ctypes.POINTER(D)], ctypes.c_int),
         "bplg_check_plan": ([PP, I32_, I64], ctypes.c_int),
         "bplg_device_status": ([ctypes.POINTER(I32_), I32_], ctypes.c_int),
@@ -358,6 +360,18 @@ def query_plan(op: int, dtype: int, n: int, batch: int) -> Plan:
     p = Plan()
     _check(lib.bplg_query_plan(op, dtype, n, batch, ctypes.byref(p)))
     return p
+
+
+def set_online_tuning(enable: bool, budget: int = 40, seed: int = 0) -> None:
+    """Spread the learned search over the calls themselves (see bplg_set_online_tuning)."""
+    _check(lib.bplg_set_online_tuning(int(bool(enable)), budget, seed))
+
+
+def online_status(op: int, dtype: int, n: int, batch: int):
+    """(evaluations, finished, best plan so far or None) of the online search for one shape."""
+    ev, fin, best = ctypes.c_int32(), ctypes.c_int32(), Plan()
+    _check(lib.bplg_online_status(op, dtype, n, batch, ctypes.byref(ev), ctypes.byref(fin), ctypes.byref(best)))
+    return ev.value, bool(fin.value), (best if best.op != 0 or best.n != 0 else None)
 
 
 def time_plan(plan: Plan, dtype: int, n: int, batch: int, reps: int = 25) -> float:

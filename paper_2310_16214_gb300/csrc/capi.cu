@@ -7,6 +7,7 @@
 #include <tuple>
 
 #include "internal.h"
+#include "online.h"
 
 namespace bplg {
 const char *last_error_cstr();
@@ -36,7 +37,8 @@ namespace {
 std::mutex g_default_mu;
 std::map<std::tuple<int, int, int, int64_t>, bplg_plan> g_default;  // (device, op, dtype, n)
 
-int resolve_plan(int op, int dtype, int64_t n, int64_t batch, const bplg_plan *given, bplg_plan *out) {
+int resolve_plan(int op, int dtype, int64_t n, int64_t batch, const bplg_plan *given, bplg_plan *out,
+                 OnlineTicket *ticket = nullptr) {
     if (given) {
         bplg_plan p = *given;
         if (p.op != op) return set_error(BPLG_ERR_INVALID_PLAN, "plan is for another operation");
@@ -48,6 +50,11 @@ int resolve_plan(int op, int dtype, int64_t n, int64_t batch, const bplg_plan *g
         return BPLG_OK;
     }
     if (cache_lookup(op, dtype, n, batch, out)) return BPLG_OK;
+    if (ticket) {
+        const int rc = online_plan(op, dtype, n, batch, out, ticket);
+        if (rc != BPLG_OK) return rc;
+        if (ticket->applies) return BPLG_OK;
+    }
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return cuda_error(e, "cudaGetDevice");
@@ -91,9 +98,14 @@ int bplg_scan_batched(int32_t dtype, const void *in, void *out, int64_t n, int64
     if (!size_ok(BPLG_OP_SCAN, n, 1)) return set_error(BPLG_ERR_UNSUPPORTED_SIZE, "scan: n must be a power of two <= 32768");
     if (!aligned16(in) || !aligned16(out)) return set_error(BPLG_ERR_INVALID_ARG, "scan: buffers must be 16-byte aligned");
     bplg_plan p;
-    int rc = resolve_plan(BPLG_OP_SCAN, dtype, n, batch, plan, &p);
+    OnlineTicket tk;
+    int rc = resolve_plan(BPLG_OP_SCAN, dtype, n, batch, plan, &p, &tk);
     if (rc != BPLG_OK) return rc;
-    return scan_launch(p, dtype, in, out, n, batch, static_cast<cudaStream_t>(stream));
+    const cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (tk.e0) cudaEventRecord(tk.e0, s);
+    rc = scan_launch(p, dtype, in, out, n, batch, s);
+    online_launched(tk, s, rc);
+    return rc;
 }
 
 int bplg_fft_batched(const void *in, void *out, int64_t n, int64_t batch, int32_t dir, const bplg_plan *plan,
@@ -105,9 +117,14 @@ int bplg_fft_batched(const void *in, void *out, int64_t n, int64_t batch, int32_
     if (!size_ok(BPLG_OP_FFT, n, 2)) return set_error(BPLG_ERR_UNSUPPORTED_SIZE, "fft: n must be a power of two in [2, 2^24]");
     if (!aligned16(in) || !aligned16(out)) return set_error(BPLG_ERR_INVALID_ARG, "fft: buffers must be 16-byte aligned");
     bplg_plan p;
-    int rc = resolve_plan(BPLG_OP_FFT, BPLG_F32, n, batch, plan, &p);
+    OnlineTicket tk;
+    int rc = resolve_plan(BPLG_OP_FFT, BPLG_F32, n, batch, plan, &p, &tk);
     if (rc != BPLG_OK) return rc;
-    return fft_launch(p, in, out, n, batch, dir, static_cast<cudaStream_t>(stream));
+    const cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (tk.e0) cudaEventRecord(tk.e0, s);
+    rc = fft_launch(p, in, out, n, batch, dir, s);
+    online_launched(tk, s, rc);
+    return rc;
 }
 
 int bplg_fft_tc_batched(const void *in, void *out, int64_t n, int64_t batch, int32_t dir, int32_t precision,
@@ -122,9 +139,14 @@ int bplg_fft_tc_batched(const void *in, void *out, int64_t n, int64_t batch, int
         return set_error(BPLG_ERR_UNSUPPORTED_SIZE, "fft tc: n must be a power of two in [512, 16384]");
     if (!aligned16(in) || !aligned16(out)) return set_error(BPLG_ERR_INVALID_ARG, "fft tc: buffers must be 16-byte aligned");
     bplg_plan p;
-    int rc = resolve_plan(BPLG_OP_FFT_TC, BPLG_F32, n, batch, plan, &p);
+    OnlineTicket tk;
+    int rc = resolve_plan(BPLG_OP_FFT_TC, BPLG_F32, n, batch, plan, &p, &tk);
     if (rc != BPLG_OK) return rc;
-    return fft_tc_launch(p, in, out, n, batch, dir, precision, static_cast<cudaStream_t>(stream));
+    const cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (tk.e0) cudaEventRecord(tk.e0, s);
+    rc = fft_tc_launch(p, in, out, n, batch, dir, precision, s);
+    online_launched(tk, s, rc);
+    return rc;
 }
 
 int bplg_tridiag_batched(const float *a, const float *b, const float *c, const float *d, float *x, int64_t n,
@@ -136,9 +158,14 @@ int bplg_tridiag_batched(const float *a, const float *b, const float *c, const f
     for (const void *q : {(const void *)a, (const void *)b, (const void *)c, (const void *)d, (const void *)x})
         if (!aligned16(q)) return set_error(BPLG_ERR_INVALID_ARG, "tridiag: buffers must be 16-byte aligned");
     bplg_plan p;
-    int rc = resolve_plan(BPLG_OP_TRIDIAG, BPLG_F32, n, batch, plan, &p);
+    OnlineTicket tk;
+    int rc = resolve_plan(BPLG_OP_TRIDIAG, BPLG_F32, n, batch, plan, &p, &tk);
     if (rc != BPLG_OK) return rc;
-    return tridiag_launch(p, a, b, c, d, x, n, batch, static_cast<cudaStream_t>(stream));
+    const cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (tk.e0) cudaEventRecord(tk.e0, s);
+    rc = tridiag_launch(p, a, b, c, d, x, n, batch, s);
+    online_launched(tk, s, rc);
+    return rc;
 }
 
 int bplg_tridiag_refined(const float *a, const float *b, const float *c, const float *d, double *x, int64_t n,
@@ -157,9 +184,14 @@ int bplg_tridiag_refined(const float *a, const float *b, const float *c, const f
     for (const void *q : {(const void *)a, (const void *)b, (const void *)c, (const void *)d})
         if (overlaps(x, total * 8, q, total * 4)) return set_error(BPLG_ERR_INVALID_ARG, "refined: x must not alias the inputs");
     bplg_plan p;
-    int rc = resolve_plan(BPLG_OP_TRIDIAG_REFINED, BPLG_F32, n, batch, plan, &p);
+    OnlineTicket tk;
+    int rc = resolve_plan(BPLG_OP_TRIDIAG_REFINED, BPLG_F32, n, batch, plan, &p, &tk);
     if (rc != BPLG_OK) return rc;
-    return tridiag_refined_launch(p, a, b, c, d, x, n, batch, max_iter, tol, iters, static_cast<cudaStream_t>(stream));
+    const cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (tk.e0) cudaEventRecord(tk.e0, s);
+    rc = tridiag_refined_launch(p, a, b, c, d, x, n, batch, max_iter, tol, iters, s);
+    online_launched(tk, s, rc);
+    return rc;
 }
 
 int bplg_arch_query(int32_t device, bplg_arch *out) {
@@ -293,6 +325,20 @@ int bplg_time_plan(const bplg_plan *plan, int32_t dtype, int64_t n, int64_t batc
     if (rc == BPLG_ERR_INVALID_PLAN) return set_error(rc, "invalid plan: " + why);
     if (rc != BPLG_OK) return rc;
     return time_plan_owned(*plan, dtype, n, batch, reps, median_ms);
+}
+
+int bplg_set_online_tuning(int32_t enable, int32_t budget, uint64_t seed) {
+    clear_error();
+    if (budget < 0) return set_error(BPLG_ERR_INVALID_ARG, "budget must be >= 0");
+    return online_set(enable != 0, budget, seed);
+}
+
+int bplg_online_status(int32_t op, int32_t dtype, int64_t n, int64_t batch, int32_t *evaluations,
+                       int32_t *finished, bplg_plan *best) {
+    clear_error();
+    if (!evaluations || !finished) return set_error(BPLG_ERR_INVALID_ARG, "null output");
+    if (max_log_for(op) < 0) return set_error(BPLG_ERR_INVALID_ARG, "unknown op");
+    return online_status(op, dtype, n, batch, evaluations, finished, best);
 }
 
 int bplg_device_status(int32_t *flag, int32_t reset) {

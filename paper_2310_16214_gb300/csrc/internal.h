@@ -86,6 +86,15 @@ int ensure_smem_attr(const void *func, int smem);
 // grid of a persistent kernel: min(work items, SMs x resident blocks per SM)
 int persistent_grid(const void *func, int threads, int smem, int64_t items, int64_t *grid);
 
+// ---- learned search in ask/tell form (tune.cu)
+struct BoSearch;
+BoSearch *bo_create(const std::vector<bplg_plan> &plans, int budget, uint64_t seed);
+int bo_next(const BoSearch *b);  // plan index to evaluate next, -1 once stopped
+void bo_tell(BoSearch *b, int i, double ms);
+int bo_best(const BoSearch *b);  // best valid plan seen, -1 if none
+int bo_evaluations(const BoSearch *b);
+void bo_destroy(BoSearch *b);
+
 // ---- plan cache (per process) and defaults
 bool cache_lookup(int op, int dtype, int64_t n, int64_t batch, bplg_plan *out);
 void cache_store(int op, int dtype, int64_t n, int64_t batch, const bplg_plan &p);

@@ -420,6 +420,139 @@ static int bo_window() {
     return w;
 }
 
+// The learned-cost-model search (Section IV-B) in ask/tell form: next()
+// names the plan to evaluate (-1 once the search has stopped) and tell()
+// records its time.  tune_search runs it in a loop; the online tuner feeds
+// it one real call at a time.
+//   * Initial design: max(5, ceil(0.6 sqrt N)) (<= 24, <= budget) plans,
+//     space-filling over the encoded knobs (the role of GPTune's
+//     Latin-hypercube start): a seeded random first plan, then each next plan
+//     the one farthest from those already chosen (largest minimum squared
+//     distance; ties broken by a seeded random order).
+//   * Then Gaussian-process expected improvement over the unevaluated plans,
+//     log time as the target, invalid plans at 10x the worst time seen,
+//     until the stopping window of evaluations without a new best, the
+//     budget, or the space runs out.
+struct BoSearch {
+    int N = 0, budget = 0, n0 = 0, window = 0;
+    std::vector<std::vector<double>> X;
+    std::vector<int> perm;
+    std::vector<double> dmin, ms;
+    std::vector<char> seen;
+    double best = INFINITY;
+    int since = 0, evals = 0, n_invalid = 0;
+    int init_next = -1;
+
+    BoSearch(const std::vector<bplg_plan> &plans, int budget_, uint64_t seed) {
+        N = static_cast<int>(plans.size());
+        budget = budget_ > 0 ? budget_ : 40;
+        SplitMix rng{seed ^ 0x5DEECE66Dull};
+        n0 = static_cast<int>(std::ceil(0.6 * std::sqrt(static_cast<double>(N))));
+        n0 = std::max(5, std::min(n0, 24));
+        n0 = std::min(std::min(n0, N), budget);
+        X = encode(plans);
+        perm.resize(N);
+        std::iota(perm.begin(), perm.end(), 0);
+        for (int i = N - 1; i > 0; --i) {
+            int j = static_cast<int>(rng.next() % uint64_t(i + 1));
+            std::swap(perm[i], perm[j]);
+        }
+        dmin.assign(N, INFINITY);
+        ms.assign(N, NAN);
+        seen.assign(N, 0);
+        window = bo_window();
+        init_next = N > 0 ? perm[0] : -1;
+    }
+
+    int next() const {
+        if (evals < n0) return init_next;
+        if (!(evals < budget && evals < N && since < window)) return -1;
+        std::vector<std::vector<double>> Xs;
+        std::vector<double> ys;
+        double ymax = -1e300;
+        for (int i = 0; i < N; ++i)
+            if (seen[i] && std::isfinite(ms[i])) ymax = std::max(ymax, std::log(ms[i]));
+        if (ymax < -1e299) ymax = 0.0;
+        for (int i = 0; i < N; ++i) {
+            if (!seen[i]) continue;
+            Xs.push_back(X[i]);
+            ys.push_back(std::isfinite(ms[i]) ? std::log(ms[i]) : ymax + std::log(10.0));
+        }
+        GP gp;
+        gp.fit(Xs, ys);
+        const double ybest = std::isfinite(best) ? (std::log(best) - gp.mean) / gp.scale : 1e9;
+        int pick = -1;
+        double pick_ei = -1.0;
+        for (int i = 0; i < N; ++i) {
+            if (seen[i]) continue;
+            double mu, sd;
+            gp.predict(X[i], &mu, &sd);
+            const double imp = ybest - mu - 0.01;
+            const double z = imp / sd;
+            const double ei = imp * norm_cdf(z) + sd * norm_pdf(z);
+            if (ei > pick_ei) {
+                pick_ei = ei;
+                pick = i;
+            }
+        }
+        return pick;
+    }
+
+    // record plan i's time (non-positive or non-finite: invalid)
+    void tell(int i, double t) {
+        if (i < 0 || i >= N || seen[i]) return;
+        if (!(t > 0.0) || !std::isfinite(t)) {
+            ++n_invalid;
+            t = INFINITY;
+        }
+        ms[i] = t;
+        seen[i] = 1;
+        ++evals;
+        if (evals <= n0) {
+            if (t < best) best = t;
+            int far = -1;
+            double far_d = -1.0;
+            for (int q = 0; q < N; ++q) {
+                const int c = perm[q];
+                if (seen[c]) continue;
+                double d2 = 0.0;
+                for (size_t f = 0; f < X[c].size(); ++f) {
+                    const double u = X[c][f] - X[i][f];
+                    d2 += u * u;
+                }
+                dmin[c] = std::min(dmin[c], d2);
+                if (dmin[c] > far_d) {
+                    far_d = dmin[c];
+                    far = c;
+                }
+            }
+            init_next = far;
+            if (far < 0) n0 = evals;  // the space is exhausted
+        } else if (t < best * (1.0 - 1e-3)) {
+            best = t;
+            since = 0;
+        } else {
+            ++since;
+        }
+    }
+
+    int best_index() const {
+        int b = -1;
+        for (int i = 0; i < N; ++i)
+            if (seen[i] && std::isfinite(ms[i]) && (b < 0 || ms[i] < ms[b])) b = i;
+        return b;
+    }
+};
+
+BoSearch *bo_create(const std::vector<bplg_plan> &plans, int budget, uint64_t seed) {
+    return new BoSearch(plans, budget, seed);
+}
+int bo_next(const BoSearch *b) { return b->next(); }
+void bo_tell(BoSearch *b, int i, double ms) { b->tell(i, ms); }
+int bo_best(const BoSearch *b) { return b->best_index(); }
+int bo_evaluations(const BoSearch *b) { return b->evals; }
+void bo_destroy(BoSearch *b) { delete b; }
+
 int tune_search(const std::vector<bplg_plan> &plans, const std::vector<int> &regs, const std::vector<int> &smem,
                 const bplg_arch &arch, int method, int budget, uint64_t seed, const CostFn &cost, int *chosen,
                 bplg_tune_report *rep) {
@@ -470,92 +603,8 @@ int tune_search(const std::vector<bplg_plan> &plans, const std::vector<int> &reg
         for (int i = 0; i < N; ++i) evaluate(i);
         *chosen = best_index();
     } else if (method == BPLG_TUNE_LEARNED) {
-        if (budget <= 0) budget = 40;
-        SplitMix rng{seed ^ 0x5DEECE66Dull};
-        // initial random design: 5 points, growing with the square root of
-        // the space (about 2 % of a 1000-plan space), within the budget
-        int n0 = static_cast<int>(std::ceil(0.6 * std::sqrt(static_cast<double>(N))));
-        n0 = std::max(5, std::min(n0, 24));
-        n0 = std::min(std::min(n0, N), budget);
-        // initial design: space-filling over the encoded knobs (the role of
-        // the Latin-hypercube start of GPTune): a seeded random first plan,
-        // then each next plan the one farthest from those already chosen
-        // (largest minimum squared distance; ties broken by a seeded random
-        // order).  Every categorical value and both ends of every numeric
-        // knob are then reached early instead of by chance.
-        const auto X = encode(plans);
-        std::vector<int> perm(N);
-        std::iota(perm.begin(), perm.end(), 0);
-        for (int i = N - 1; i > 0; --i) {
-            int j = static_cast<int>(rng.next() % uint64_t(i + 1));
-            std::swap(perm[i], perm[j]);
-        }
-        std::vector<double> dmin(N, INFINITY);
-        double best = INFINITY;
-        int since = 0;
-        int next = perm[0];
-        for (int k = 0; k < n0; ++k) {
-            double t = evaluate(next);
-            if (t < best) best = t;
-            int far = -1;
-            double far_d = -1.0;
-            for (int q = 0; q < N; ++q) {
-                const int i = perm[q];
-                if (seen[i]) continue;
-                double d2 = 0.0;
-                for (size_t f = 0; f < X[i].size(); ++f) {
-                    const double u = X[i][f] - X[next][f];
-                    d2 += u * u;
-                }
-                dmin[i] = std::min(dmin[i], d2);
-                if (dmin[i] > far_d) {
-                    far_d = dmin[i];
-                    far = i;
-                }
-            }
-            if (far < 0) break;
-            next = far;
-        }
-        const int window = bo_window();
-        while (r.evaluations < budget && r.evaluations < N && since < window) {
-            // training set: log time, invalid points at a high penalty
-            std::vector<std::vector<double>> Xs;
-            std::vector<double> ys;
-            double ymax = -1e300;
-            for (int i = 0; i < N; ++i)
-                if (seen[i] && std::isfinite(ms[i])) ymax = std::max(ymax, std::log(ms[i]));
-            if (ymax < -1e299) ymax = 0.0;
-            for (int i = 0; i < N; ++i) {
-                if (!seen[i]) continue;
-                Xs.push_back(X[i]);
-                ys.push_back(std::isfinite(ms[i]) ? std::log(ms[i]) : ymax + std::log(10.0));
-            }
-            GP gp;
-            gp.fit(Xs, ys);
-            const double ybest = std::isfinite(best) ? (std::log(best) - gp.mean) / gp.scale : 1e9;
-            int pick = -1;
-            double pick_ei = -1.0;
-            for (int i = 0; i < N; ++i) {
-                if (seen[i]) continue;
-                double mu, sd;
-                gp.predict(X[i], &mu, &sd);
-                const double imp = ybest - mu - 0.01;
-                const double z = imp / sd;
-                const double ei = imp * norm_cdf(z) + sd * norm_pdf(z);
-                if (ei > pick_ei) {
-                    pick_ei = ei;
-                    pick = i;
-                }
-            }
-            if (pick < 0) break;
-            const double t = evaluate(pick);
-            if (t < best * (1.0 - 1e-3)) {
-                best = t;
-                since = 0;
-            } else {
-                ++since;
-            }
-        }
+        BoSearch bo(plans, budget, seed);
+        for (int i = bo.next(); i >= 0; i = bo.next()) bo.tell(i, evaluate(i));
         *chosen = best_index();
     } else {
         if (rep) *rep = r;
