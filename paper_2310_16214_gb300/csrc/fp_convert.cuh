@@ -12,6 +12,7 @@
 //
 //   widen_f32(f)           exact float -> double (every finite value, ±0, ±inf,
 //                          NaN stays NaN)
+//   widen_f32_normal(f)    the same for zero or normal f (fewer operations)
 //   widen_f32_pow2(f, k)   exact f * 2^k as a double, for |k| <= 700
 //   narrow_f64(x)          double -> float rounded to nearest, ties to even,
 //                          with overflow to ±inf and gradual underflow
@@ -103,6 +104,21 @@ BPLG_FPC double widen_f32_pow2(float f, int k) {
 }
 
 BPLG_FPC double widen_f32(float f) { return widen_f32_pow2(f, 0); }
+
+// widen_f32 for a float known to be zero or normal (no subnormal, inf or
+// NaN): the exponent rebias and the zero case only.
+BPLG_FPC double widen_f32_normal(float f) {
+    const uint32_t u = bits_f32(f);
+    const uint32_t a = u & 0x7FFFFFFFu;
+    const uint32_t hi = (u & 0x80000000u) | (a ? (a >> 3) + (896u << 20) : 0u);
+    return f64_from_halves(hi, u << 29);
+}
+
+// true when f is zero or normal (widen_f32_normal applies)
+BPLG_FPC bool f32_zero_or_normal(float f) {
+    const uint32_t e = bits_f32(f) & 0x7F800000u;
+    return (bits_f32(f) & 0x7FFFFFFFu) == 0u || (e != 0u && e != 0x7F800000u);
+}
 
 // double -> float, round to nearest even.  The 52-bit fraction splits into
 // the 23 kept bits and 29 dropped ones; the dropped part decides the

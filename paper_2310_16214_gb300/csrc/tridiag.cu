@@ -35,6 +35,7 @@
 // coefficients are also cached as float64 in shared memory, so the residual
 // needs no conversions (the float64 pipe is the bottleneck of this kernel).
 #include <cmath>
+#include <type_traits>
 
 #include "device_util.cuh"
 #include "fp_convert.cuh"
@@ -603,6 +604,24 @@ __device__ __forceinline__ float system_max(float v, float *red, int wps) {
     return r;
 }
 
+// system_max with one barrier: red holds two sets of warp slots (64 floats)
+// used alternately (ph toggles every call), so a call's writes never meet
+// the previous call's reads -- every thread passes this call's barrier only
+// after finishing the reads of the one before.
+__device__ __forceinline__ float system_max1(float v, float *red, int wps, int &ph) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(kFullMask, v, o));
+    float *slot = red + (ph & 1) * 32;
+    ph ^= 1;
+    const int warp = threadIdx.x >> 5;
+    if ((threadIdx.x & 31) == 0) slot[warp] = v;
+    __syncthreads();
+    const int w0 = warp - (warp & (wps - 1));
+    float r = slot[w0];
+    for (int k = 1; k < wps; ++k) r = fmaxf(r, slot[w0 + k]);
+    return r;
+}
+
 // 2^e as float64 and float32, built from the exponent bits (exact).
 __device__ __forceinline__ double pow2_f64(int e) {
     return __longlong_as_double(static_cast<long long>(1023 + e) << 52);
@@ -811,7 +830,7 @@ __global__ void __launch_bounds__(MAXT)
     constexpr int PF = CO == 0 ? P : 1;  // float32 coefficient registers (layout 4)
     constexpr int PD = CO == 1 ? P : 1;  // float64 coefficient registers (layout 5)
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    __shared__ float red[32];
+    __shared__ float red[64];
     __shared__ int done_sys[32];
     const int n = 1 << logn;
     const int tps = 1 << log_tps;
@@ -853,6 +872,14 @@ __global__ void __launch_bounds__(MAXT)
     float oa[PF], ob[PF], oc[PF], od[PF];
     double ca[PD], cb[PD], cc[PD], cd[PD];
     float dmin = 3.0e38f;
+    // every coefficient of the block zero or normal (the usual case): the
+    // residuals widen them with the short form
+    bool normal = true;
+#pragma unroll
+    for (int i = 0; i < P; ++i)
+        normal = normal && fpc::f32_zero_or_normal(la[i]) && fpc::f32_zero_or_normal(lb[i]) &&
+                 fpc::f32_zero_or_normal(lc[i]) && fpc::f32_zero_or_normal(ld[i]);
+    const bool fast = __syncthreads_and(normal) != 0;
 #pragma unroll
     for (int i = 0; i < P; ++i) {
         dmin = fminf(dmin, fabsf(lb[i]) - fabsf(la[i]) - fabsf(lc[i]));
@@ -873,6 +900,7 @@ __global__ void __launch_bounds__(MAXT)
     }
     // la..ld become the working copy
     if (t == 0) done_sys[s] = valid ? 0 : 1;
+    const bool single = spb == 1;  // (then the block's one system is valid)
     cr_register_solve<P, PAD, SHUFFLE>(la, lb, lc, ld, log_m, log_tps, t, rows, bnd);
     double xs[P];
     float xmaxf = 0.f;
@@ -881,9 +909,10 @@ __global__ void __launch_bounds__(MAXT)
         xs[i] = fpc::widen_f32(ld[i]);
         xmaxf = fmaxf(xmaxf, fabsf(ld[i]));
     }
-    xmaxf = system_max(xmaxf, red, wps);
+    int ph = 0;
+    xmaxf = system_max1(xmaxf, red, wps, ph);
     // diagonal-dominance margin (see the shared-memory refinement)
-    dmin = -system_max(-dmin, red, wps);
+    dmin = -system_max1(-dmin, red, wps, ph);
     const float dmarg = dmin > 0.f ? dmin * (1.0f - 1e-5f) : 0.f;
     // right-hand sides of the stopping tests below: 0 (never stop) unless
     // comfortably above the float32 subnormal range
@@ -902,44 +931,55 @@ __global__ void __launch_bounds__(MAXT)
         // widening and narrowing are integer operations, so the FP64 pipe
         // carries only the three fused multiply-adds per equation
         float rmaxf = 0.f;
+        auto residual = [&](auto fast_tag) {
+            constexpr bool FAST = decltype(fast_tag)::value;
+            auto widen = [](float f) { return FAST ? fpc::widen_f32_normal(f) : fpc::widen_f32(f); };
 #pragma unroll
-        for (int i = 0; i < P; ++i) {
-            const double xl = i > 0 ? xs[i > 0 ? i - 1 : 0] : xl_nb;
-            const double xr = i < P - 1 ? xs[i < P - 1 ? i + 1 : 0] : xr_nb;
-            double r;
-            if constexpr (CO == 1) {
-                r = fma(-ca[i], xl, cd[i]);
-                r = fma(-cb[i], xs[i], r);
-                r = fma(-cc[i], xr, r);
-                const float4 q = ocoef[i * blockDim.x];
-                la[i] = q.x;
-                lb[i] = q.y;
-                lc[i] = q.z;
-            } else if constexpr (CO == 2) {
-                const float4 q = ocoef[i * blockDim.x];
-                r = fma(-fpc::widen_f32(q.x), xl, fpc::widen_f32(q.w));
-                r = fma(-fpc::widen_f32(q.y), xs[i], r);
-                r = fma(-fpc::widen_f32(q.z), xr, r);
-                la[i] = q.x;
-                lb[i] = q.y;
-                lc[i] = q.z;
-            } else {
-                r = fma(-fpc::widen_f32(oa[i]), xl, fpc::widen_f32(od[i]));
-                r = fma(-fpc::widen_f32(ob[i]), xs[i], r);
-                r = fma(-fpc::widen_f32(oc[i]), xr, r);
-                la[i] = oa[i];
-                lb[i] = ob[i];
-                lc[i] = oc[i];
+            for (int i = 0; i < P; ++i) {
+                const double xl = i > 0 ? xs[i > 0 ? i - 1 : 0] : xl_nb;
+                const double xr = i < P - 1 ? xs[i < P - 1 ? i + 1 : 0] : xr_nb;
+                double r;
+                if constexpr (CO == 1) {
+                    r = fma(-ca[i], xl, cd[i]);
+                    r = fma(-cb[i], xs[i], r);
+                    r = fma(-cc[i], xr, r);
+                    const float4 q = ocoef[i * blockDim.x];
+                    la[i] = q.x;
+                    lb[i] = q.y;
+                    lc[i] = q.z;
+                } else if constexpr (CO == 2) {
+                    const float4 q = ocoef[i * blockDim.x];
+                    r = fma(-widen(q.x), xl, widen(q.w));
+                    r = fma(-widen(q.y), xs[i], r);
+                    r = fma(-widen(q.z), xr, r);
+                    la[i] = q.x;
+                    lb[i] = q.y;
+                    lc[i] = q.z;
+                } else {
+                    r = fma(-widen(oa[i]), xl, widen(od[i]));
+                    r = fma(-widen(ob[i]), xs[i], r);
+                    r = fma(-widen(oc[i]), xr, r);
+                    la[i] = oa[i];
+                    lb[i] = ob[i];
+                    lc[i] = oc[i];
+                }
+                const float rf = fpc::narrow_f64_ftz(r);
+                rmaxf = fmaxf(rmaxf, fabsf(rf));
+                ld[i] = rf;
             }
-            const float rf = fpc::narrow_f64_ftz(r);
-            rmaxf = fmaxf(rmaxf, fabsf(rf));
-            ld[i] = rf;
-        }
-        rmaxf = system_max(rmaxf, red, wps);
-        if (t == 0 && rmaxf * (1.0f + 1e-5f) <= varah_rhs)
-            done_sys[s] = 1;
-        __syncthreads();
-        {
+        };
+        if (fast)
+            residual(std::true_type{});
+        else
+            residual(std::false_type{});
+        rmaxf = system_max1(rmaxf, red, wps, ph);
+        if (single) {
+            // one system per block: every thread holds the same maxima and
+            // takes the same decision, no flags or barriers needed
+            if (rmaxf * (1.0f + 1e-5f) <= varah_rhs || k == max_iter) break;
+        } else {
+            if (t == 0 && rmaxf * (1.0f + 1e-5f) <= varah_rhs) done_sys[s] = 1;
+            __syncthreads();
             int all_done = 1;
             for (int q = 0; q < spb; ++q) all_done &= done_sys[q];
             __syncthreads();
@@ -952,22 +992,26 @@ __global__ void __launch_bounds__(MAXT)
 #pragma unroll
         for (int i = 0; i < P; ++i) ld[i] *= sigma;
         cr_register_solve<P, PAD, SHUFFLE>(la, lb, lc, ld, log_m, log_tps, t, rows, bnd);
-        const bool was_done = done_sys[s] != 0 || rmaxf == 0.f;
+        const bool was_done = (!single && done_sys[s] != 0) || rmaxf == 0.f;
         float emaxf = 0.f;
 #pragma unroll
         for (int i = 0; i < P; ++i) {
             if (!was_done) xs[i] += fpc::widen_f32_pow2(ld[i], ex);
             emaxf = fmaxf(emaxf, fabsf(ld[i]));
         }
-        emaxf = system_max(emaxf, red, wps);
+        emaxf = system_max1(emaxf, red, wps, ph);
         if (!was_done) ++applied;
-        if (t == 0 && (was_done || emaxf * pow2_f32(ex) * (1.0f + 1e-5f) <= corr_rhs))
-            done_sys[s] = 1;
-        __syncthreads();
-        int all_done = 1;
-        for (int q = 0; q < spb; ++q) all_done &= done_sys[q];
-        __syncthreads();
-        if (all_done) break;
+        const bool small = was_done || emaxf * pow2_f32(ex) * (1.0f + 1e-5f) <= corr_rhs;
+        if (single) {
+            if (small) break;
+        } else {
+            if (t == 0 && small) done_sys[s] = 1;
+            __syncthreads();
+            int all_done = 1;
+            for (int q = 0; q < spb; ++q) all_done &= done_sys[q];
+            __syncthreads();
+            if (all_done) break;
+        }
     }
     if (valid) {
 #pragma unroll

@@ -27,6 +27,14 @@ static void widen_case(uint32_t u, int k) {
         if (fails++ < 10) std::printf("widen %08x k=%d: got %016llx want %016llx\n", u, k,
                                       (unsigned long long)bits64(got), (unsigned long long)bits64(ref));
     }
+    // the zero-or-normal form, and the predicate that selects it
+    const bool zn = f == 0.0f || std::isnormal(f);
+    if (fpc::f32_zero_or_normal(f) != zn) {
+        if (fails++ < 10) std::printf("zero_or_normal %08x: got %d\n", u, int(!zn));
+    }
+    if (zn && k == 0 && bits64(fpc::widen_f32_normal(f)) != bits64(static_cast<double>(f))) {
+        if (fails++ < 10) std::printf("widen_normal %08x\n", u);
+    }
 }
 static void narrow_case(uint64_t v) {
     const double x = from64(v);

@@ -118,6 +118,22 @@ def test_refined_at_the_target_tolerance(bp):
     assert it.min() >= 1
 
 
+def test_refined_with_subnormal_coefficients(bp):
+    # systems with subnormal and zero off-diagonal coefficients take the
+    # general float -> double widening; every register plan still meets 1e-12
+    n, batch = 1024, 6
+    a, b, c, d, _ = si.tridiag_f32(batch, n, stream=79)
+    a[1, 5::7] = np.float32(3e-39)   # subnormal
+    c[3, 2::11] = np.float32(-1e-40)  # subnormal
+    a[4, 1::3] = 0.0
+    sysm = (a, b, c, d)
+    ref = oracle.thomas(a, b, c, d)
+    for p in bp.enumerate_plans(bp.OP_TRIDIAG_REFINED, bp.F32, n):
+        if p.smem_layout >= 4:
+            x, it = run_refined(bp, sysm, p)
+            assert tri_rel_err(x, ref).max() <= 1e-12, p
+
+
 def test_refined_zero_iterations_is_the_float32_solve(bp):
     n, batch = 256, 4
     sysm = si.tridiag_f32(batch, n, stream=77)
