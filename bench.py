@@ -76,12 +76,10 @@ def read_peaks():
 # batch, doubled; keyed by row and plan.  A launch whose plan was not captured
 # reports null.
 NCU_TRAFFIC = {
-    # tridiag_refined_reg_kernel, layout 6: DRAM read + write per half-size
-    # launch, doubled (the rest of x is still in L2 at kernel end)
+    # tridiag_refined_reg_kernel, layout 6, P = 16: DRAM read + write of one
+    # half-size launch, doubled (the rest of x is still in L2 at kernel end)
     ("refined_1024", (("P", 16), ("L", 64), ("spb", 1), ("shuffle", 1), ("pattern", 0), ("smem_layout", 6),
-                      ("smem_pad", 0), ("io", 0), ("cr_switch", 32))): 2 * (134301696 + 27660288),
-    ("refined_1024", (("P", 8), ("L", 128), ("spb", 1), ("shuffle", 1), ("pattern", 0), ("smem_layout", 6),
-                      ("smem_pad", 0), ("io", 0), ("cr_switch", 32))): 2 * (134287872 + 28645888),
+                      ("smem_pad", 0), ("io", 0), ("cr_switch", 32))): 2 * (134331648 + 26756608),
 }
 
 # FP64 issue rate of one SM: 2 double-precision fused multiply-adds per clock
@@ -768,6 +766,7 @@ def tune_report(args):
     peak, _ = read_peaks()
     cases = [("fft", bp.OP_FFT, bp.F32, n, FFT_TOTAL // n, 16) for n in FFT_SIZES]
     cases += [("tridiag", bp.OP_TRIDIAG, bp.F32, n, TRI_TOTAL // n, 20) for n in TRI_SIZES]
+    cases += [("tridiag_wm", bp.OP_TRIDIAG_WM, bp.F32, n, TRI_TOTAL // n, 20) for n in TRI_SIZES]
     cases += [("refined", bp.OP_TRIDIAG_REFINED, bp.F32, REF_N, REF_BATCH, 24)]
     cases += [("scan_i32", bp.OP_SCAN, bp.I32, n, SCAN_TOTAL // n, 8) for n in SCAN_SIZES]
     cases += [("scan_f32", bp.OP_SCAN, bp.F32, n, SCAN_TOTAL // n, 8) for n in SCAN_SIZES]

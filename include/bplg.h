@@ -63,7 +63,8 @@ typedef enum {
     BPLG_OP_FFT = 1,             /* Section III, Stockham FFT */
     BPLG_OP_TRIDIAG = 2,         /* Section III, tridiagonal solver (CR/PCR hybrid) */
     BPLG_OP_TRIDIAG_REFINED = 3, /* the solver inside float64-residual refinement */
-    BPLG_OP_FFT_TC = 4           /* FFT whose radix-16 stages run on tensor cores */
+    BPLG_OP_FFT_TC = 4,          /* FFT whose radix-16 stages run on tensor cores */
+    BPLG_OP_TRIDIAG_WM = 5       /* Section III, tridiagonal solver of Wang and Mou (divide and conquer) */
 } bplg_op;
 
 typedef enum { BPLG_PATTERN_KS = 0, BPLG_PATTERN_LF = 1 } bplg_scan_pattern;
@@ -79,9 +80,13 @@ typedef enum { BPLG_TC_BF16 = 0, BPLG_TC_F16 = 1 } bplg_tc_precision;
  *   L       threads per block = spb * (n / P).
  *   spb     problems (signals or systems) per block.
  *   S       shared-memory elements per block (derived, reported).
- *   radix   FFT radix r in {2,4,8,16}; 2 for scan and tridiag.
+ *   radix   FFT radix r in {2,4,8,16}; Wang-Mou tridiag: runs merged per
+ *           stage, r in {2,4,8} (r <= n / P unless n = P); 2 for scan and
+ *           the CR/PCR tridiag.
  *   shuffle tridiag: the PCR phase runs in one warp with shuffles (cr_switch
- *           <= 32); scan: always 1 (warp-shuffle prefix stages).
+ *           <= 32); Wang-Mou: merge stages whose groups fit in a warp
+ *           exchange by shuffles (else every stage goes through shared
+ *           memory); scan: always 1 (warp-shuffle prefix stages).
  *   pattern scan: prefix circuit of the shuffle stages, BPLG_PATTERN_KS or
  *           BPLG_PATTERN_LF (Fig. 1(f) / 1(d)).
  *   smem_layout FFT: 0 interleaved complex, 1 real and imaginary parts
@@ -206,9 +211,16 @@ int bplg_fft_batched_noalloc(const void *in, void *out, int64_t n, int64_t batch
                              const bplg_plan *plan, void *stream);
 
 /* Batched tridiagonal solve (Section III, "Tridiagonal system solvers"):
- * a_i x_{i-1} + b_i x_i + c_i x_{i+1} = d_i for every system, by cyclic
- * reduction down to plan->cr_switch equations, parallel cyclic reduction on
- * those, and CR back substitution; all in float32 shared memory.
+ * a_i x_{i-1} + b_i x_i + c_i x_{i+1} = d_i for every system.  The plan's op
+ * picks the solver:
+ *   BPLG_OP_TRIDIAG (and plan NULL): cyclic reduction down to
+ *           plan->cr_switch equations, parallel cyclic reduction on those,
+ *           and CR back substitution; all in float32.
+ *   BPLG_OP_TRIDIAG_WM: the divide-and-conquer method of Wang and Mou (the
+ *           WM pattern of Fig. 1(e)): each thread solves its P equations for
+ *           their two outer neighbours (one Thomas sweep, three right-hand
+ *           sides), then merge stages of radix plan->radix join adjacent
+ *           runs until one run covers the system; float32.
  *   a,b,c,d device, float32 [batch][n] each (structure of arrays);
  *           a[s][0] and c[s][n-1] are never read.
  *   x       device, float32 [batch][n]; may alias d.

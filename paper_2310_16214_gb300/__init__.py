@@ -27,7 +27,7 @@ ERR_DEVICE_FLAG = -6
 ERR_NO_DEVICE = -7
 
 I32, F32 = 0, 1
-OP_SCAN, OP_FFT, OP_TRIDIAG, OP_TRIDIAG_REFINED, OP_FFT_TC = 0, 1, 2, 3, 4
+OP_SCAN, OP_FFT, OP_TRIDIAG, OP_TRIDIAG_REFINED, OP_FFT_TC, OP_TRIDIAG_WM = 0, 1, 2, 3, 4, 5
 PATTERN_KS, PATTERN_LF = 0, 1
 TUNE_ANALYTIC, TUNE_LEARNED, TUNE_EXHAUSTIVE = 0, 1, 2
 TC_BF16, TC_F16 = 0, 1

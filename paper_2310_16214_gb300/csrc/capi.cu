@@ -157,13 +157,16 @@ int bplg_tridiag_batched(const float *a, const float *b, const float *c, const f
     if (!size_ok(BPLG_OP_TRIDIAG, n, 2)) return set_error(BPLG_ERR_UNSUPPORTED_SIZE, "tridiag: n must be a power of two in [2, 8192]");
     for (const void *q : {(const void *)a, (const void *)b, (const void *)c, (const void *)d, (const void *)x})
         if (!aligned16(q)) return set_error(BPLG_ERR_INVALID_ARG, "tridiag: buffers must be 16-byte aligned");
+    // the plan's op picks the solver: CR/PCR hybrid (default) or Wang-Mou
+    const int op = plan && plan->op == BPLG_OP_TRIDIAG_WM ? BPLG_OP_TRIDIAG_WM : BPLG_OP_TRIDIAG;
     bplg_plan p;
     OnlineTicket tk;
-    int rc = resolve_plan(BPLG_OP_TRIDIAG, BPLG_F32, n, batch, plan, &p, &tk);
+    int rc = resolve_plan(op, BPLG_F32, n, batch, plan, &p, &tk);
     if (rc != BPLG_OK) return rc;
     const cudaStream_t s = static_cast<cudaStream_t>(stream);
     if (tk.e0) cudaEventRecord(tk.e0, s);
-    rc = tridiag_launch(p, a, b, c, d, x, n, batch, s);
+    rc = op == BPLG_OP_TRIDIAG_WM ? tridiag_wm_launch(p, a, b, c, d, x, n, batch, s)
+                                  : tridiag_launch(p, a, b, c, d, x, n, batch, s);
     online_launched(tk, s, rc);
     return rc;
 }

@@ -439,10 +439,11 @@ __global__ void __launch_bounds__(MAXT)
 // (n = 16384: 1024 threads, one block per SM) keep a load in flight.
 template <int LOGN>
 struct SplitRing {
-    // slots that fit beside the exchange buffer of one signal in 227 KB
-    static constexpr int kSlotBytes = (1 << LOGN) * 8;
-    static constexpr int kExchBytes = ((1 << LOGN) + (1 << LOGN) / 32) * 4;
-    static constexpr int NS = (2 * kSlotBytes + kExchBytes <= 227 * 1024) ? 2 : 1;
+    // One slot: it is refilled as soon as the first stage has read it, so
+    // the next tile's copy already overlaps the remaining stages, and the
+    // block keeps the shared-memory footprint (and occupancy) of a single
+    // tile plus its exchange buffer.
+    static constexpr int NS = 1;
 };
 
 template <int LOGN, int DIR, int MAXT>

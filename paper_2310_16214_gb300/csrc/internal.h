@@ -65,6 +65,11 @@ int fft_large_launch(const bplg_plan &p, const void *in, void *out, int64_t n, i
 bool tridiag_launch_info(const bplg_plan &p, int64_t n, int64_t batch, bool refined, Launch *out);
 int tridiag_launch(const bplg_plan &p, const float *a, const float *b, const float *c,
                    const float *d, float *x, int64_t n, int64_t batch, cudaStream_t s);
+// Wang-Mou divide-and-conquer solver (tridiag_wm.cu)
+int tridiag_wm_smem_bytes(const bplg_plan &p, int64_t n);
+bool tridiag_wm_launch_info(const bplg_plan &p, int64_t n, int64_t batch, Launch *out);
+int tridiag_wm_launch(const bplg_plan &p, const float *a, const float *b, const float *c, const float *d, float *x,
+                      int64_t n, int64_t batch, cudaStream_t s);
 int tridiag_refined_launch(const bplg_plan &p, const float *a, const float *b, const float *c,
                            const float *d, double *x, int64_t n, int64_t batch, int max_iter,
                            double tol, int32_t *iters, cudaStream_t s);

@@ -68,6 +68,7 @@ int max_log_for(int op) {
         case BPLG_OP_FFT: return kFftLargeMaxLog;
         case BPLG_OP_TRIDIAG: return kTridiagMaxLog;
         case BPLG_OP_TRIDIAG_REFINED: return kRefinedMaxLog;
+        case BPLG_OP_TRIDIAG_WM: return kTridiagMaxLog;
         case BPLG_OP_FFT_TC: return kFftMaxLog;
         default: return -1;
     }
@@ -110,6 +111,15 @@ bool plan_structurally_valid(const bplg_plan &p, int dtype, int64_t n, std::stri
                 return fail(why, "tensor-core FFT: padded interleaved layout; io 0 (tcgen05) or 1 (mma.sync)");
             if (p.io == 0 && (n < 1024 || n > 16384 || p.L % 128 != 0))
                 return fail(why, "tensor-core FFT with tcgen05: 1024 <= n <= 16384 and blocks of 128-thread tiles");
+            return true;
+        case BPLG_OP_TRIDIAG_WM:
+            if (n < 2) return fail(why, "Wang-Mou: n >= 2");
+            if (p.P < 2 || p.P > 16) return fail(why, "Wang-Mou: 2 <= P <= 16");
+            if (p.radix != 2 && p.radix != 4 && p.radix != 8) return fail(why, "Wang-Mou: radix must be 2, 4 or 8");
+            if (tps > 1 && p.radix > tps) return fail(why, "Wang-Mou: radix <= n / P");
+            if (p.shuffle < 0 || p.shuffle > 1) return fail(why, "Wang-Mou: shuffle is 0 or 1");
+            if (p.pattern != 0 || p.smem_layout != 0 || p.smem_pad != 0 || p.io != 0 || p.cr_switch != 0)
+                return fail(why, "Wang-Mou: pattern, smem_layout, smem_pad, io and cr_switch are 0");
             return true;
         case BPLG_OP_TRIDIAG:
         case BPLG_OP_TRIDIAG_REFINED: {
@@ -154,6 +164,7 @@ int plan_smem_bytes(const bplg_plan &p, int dtype, int64_t n) {
             return tridiag_smem_bytes(p.smem_pad, n, p.spb, false, p.smem_layout, p.io, ilog2(p.cr_switch), p.P);
         case BPLG_OP_TRIDIAG_REFINED:
             return tridiag_smem_bytes(p.smem_pad, n, p.spb, true, p.smem_layout, 0, ilog2(p.cr_switch), p.P);
+        case BPLG_OP_TRIDIAG_WM: return tridiag_wm_smem_bytes(p, n);
         default: return 0;
     }
 }
@@ -193,6 +204,10 @@ void plan_finalize(bplg_plan *p, int dtype, int64_t n) {
             if (p->op == BPLG_OP_TRIDIAG_REFINED) p->io = 0;
             p->S = static_cast<int32_t>(p->spb * n);
             break;
+        case BPLG_OP_TRIDIAG_WM:
+            p->pattern = p->smem_layout = p->smem_pad = p->io = p->cr_switch = 0;
+            p->S = plan_smem_bytes(*p, dtype, n) > 0 ? p->L : 0;  // descriptor slots
+            break;
         default:
             break;
     }
@@ -223,6 +238,14 @@ std::vector<bplg_plan> enumerate_structural(int op, int dtype, int64_t n) {
                 for (int pat = 0; pat <= 1; ++pat) {
                     p.pattern = pat;
                     push(p);
+                }
+            } else if (op == BPLG_OP_TRIDIAG_WM) {
+                for (int r = 8; r >= 2; r /= 2) {
+                    for (int sh = 1; sh >= 0; --sh) {
+                        p.radix = r;
+                        p.shuffle = sh;
+                        push(p);
+                    }
                 }
             } else if (op == BPLG_OP_FFT_TC) {
                 if (P != 16) continue;
@@ -334,6 +357,7 @@ bool launch_info_for(const bplg_plan &p, int dtype, int64_t n, Launch *li) {
             return fft_launch_info(p, n, 1, -1, li);
         case BPLG_OP_TRIDIAG: return tridiag_launch_info(p, n, 1, false, li);
         case BPLG_OP_TRIDIAG_REFINED: return tridiag_launch_info(p, n, 1, true, li);
+        case BPLG_OP_TRIDIAG_WM: return tridiag_wm_launch_info(p, n, 1, li);
         case BPLG_OP_FFT_TC: return fft_tc_launch_info(p, n, 1, BPLG_TC_BF16, -1, li);
         default: return false;
     }

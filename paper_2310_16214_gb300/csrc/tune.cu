@@ -225,7 +225,7 @@ int analytic_plan(int op, int dtype, int64_t n, bplg_plan *out) {
     if (plans.empty()) return set_error(BPLG_ERR_UNSUPPORTED_SIZE, "no valid plan for this size");
     std::vector<bplg_candidate> c;
     for (size_t i = 0; i < plans.size(); ++i) c.push_back(to_candidate(plans[i], regs[i], smem[i]));
-    int k = guideline_select(a, c.data(), static_cast<int>(c.size()), op == BPLG_OP_FFT);
+    int k = guideline_select(a, c.data(), static_cast<int>(c.size()), op == BPLG_OP_FFT || op == BPLG_OP_TRIDIAG_WM);
     if (k < 0) return set_error(BPLG_ERR_UNSUPPORTED_SIZE, "no plan can launch");
     *out = plans[k];
     return BPLG_OK;
@@ -252,6 +252,9 @@ std::vector<double> raw_features(const bplg_plan &p) {
                              double(p.smem_pad), std::log2(double(std::max(1, p.cr_switch))), double(p.shuffle)};
     for (int k = 0; k < 7; ++k) f.push_back(p.smem_layout == k ? 1.0 : 0.0);
     for (int k = 0; k < 3; ++k) f.push_back(p.io == k ? 1.0 : 0.0);
+    // the merge radix of the Wang-Mou solver (a constant column elsewhere,
+    // dropped by the normalisation)
+    f.push_back(p.op == BPLG_OP_TRIDIAG_WM ? std::log2(double(p.radix)) : 0.0);
     return f;
 }
 
@@ -665,6 +668,10 @@ int launch_plan(const bplg_plan &p, int dtype, int64_t n, int64_t batch, void *i
             return tridiag_launch(p, static_cast<const float *>(in), static_cast<const float *>(b),
                                   static_cast<const float *>(c), static_cast<const float *>(d),
                                   static_cast<float *>(out), n, batch, s);
+        case BPLG_OP_TRIDIAG_WM:
+            return tridiag_wm_launch(p, static_cast<const float *>(in), static_cast<const float *>(b),
+                                     static_cast<const float *>(c), static_cast<const float *>(d),
+                                     static_cast<float *>(out), n, batch, s);
         case BPLG_OP_TRIDIAG_REFINED:
             return tridiag_refined_launch(p, static_cast<const float *>(in), static_cast<const float *>(b),
                                           static_cast<const float *>(c), static_cast<const float *>(d),
@@ -741,7 +748,7 @@ struct TimingArena {
         const size_t osz = (cplx || op == BPLG_OP_TRIDIAG_REFINED) ? 8 : 4;
         if ((e = cudaMalloc(&tb.in, total * esz)) != cudaSuccess) return cuda_error(e, "timing buffers");
         if ((e = cudaMalloc(&tb.out, total * osz)) != cudaSuccess) return cuda_error(e, "timing buffers");
-        if (op == BPLG_OP_TRIDIAG || op == BPLG_OP_TRIDIAG_REFINED) {
+        if (op == BPLG_OP_TRIDIAG || op == BPLG_OP_TRIDIAG_REFINED || op == BPLG_OP_TRIDIAG_WM) {
             if ((e = cudaMalloc(&tb.b, total * 4)) != cudaSuccess) return cuda_error(e, "timing buffers");
             if ((e = cudaMalloc(&tb.c, total * 4)) != cudaSuccess) return cuda_error(e, "timing buffers");
             if ((e = cudaMalloc(&tb.d, total * 4)) != cudaSuccess) return cuda_error(e, "timing buffers");
