@@ -147,7 +147,11 @@ typedef struct {
  * problem s, out[s][i] = in[s][0] + ... + in[s][i].
  *   dtype  BPLG_I32 (two's-complement wrap-around, bit-exact) or BPLG_F32.
  *   in,out device, [batch][n] of dtype; in == out (in place) is allowed.
- *   n      power of two, 1 <= n <= 32768; batch >= 1.
+ *   n      1 <= n <= 32768; batch >= 1.  A power of two runs its own plan;
+ *          any other n runs the plan of the next power of two n' (plan->n ==
+ *          n', or plan NULL), the rows read as if padded with zeros to n'
+ *          (element-wise accesses; rows stay n apart, nothing past n is
+ *          written).
  * Errors: INVALID_ARG, UNSUPPORTED_SIZE, INVALID_PLAN, CUDA. */
 int bplg_scan_batched(int32_t dtype, const void *in, void *out, int64_t n, int64_t batch,
                       const bplg_plan *plan, void *stream);
@@ -157,11 +161,21 @@ int bplg_scan_batched(int32_t dtype, const void *in, void *out, int64_t n, int64
  * with dir = -1 (forward) or +1 (inverse, unnormalised), natural order.
  *   in,out device, [batch][n] complex64 as interleaved (re, im) float pairs;
  *          in == out is allowed.
- *   n      power of two, 2 <= n <= 2^24; batch >= 1.  Above 16384 points the
- *          transform runs as two kernels (see n1_log in the plan) through a
- *          scratch buffer of n * batch complex values that the library
- *          allocates on first use per device and grows when needed (a growth
- *          synchronises the device); in may equal out.
+ *   n      2 <= n <= 2^24 (at most 2^23 when n is not a power of two);
+ *          batch >= 1.  Above 16384 points the transform runs as two kernels
+ *          (see n1_log in the plan) through a scratch buffer of n * batch
+ *          complex values that the library allocates on first use per device
+ *          and stream and grows when needed (a growth waits for the stream);
+ *          in may equal out.
+ *          A length that is not a power of two runs Bluestein's chirp
+ *          identity: X_k = h_k sum_j (x_j h_j) conj(h_{k-j}) with
+ *          h_m = exp(dir pi i m^2 / n), a cyclic convolution of length
+ *          M = next power of two >= 2n - 1 computed with two M-point FFTs
+ *          (plan: a plan for M, or NULL) and three elementwise kernels,
+ *          through a scratch of M * batch complex values per device and
+ *          stream.  The chirp and the transformed chirp are per-(n, dir)
+ *          tables made on the first call with that n (float64 on the host,
+ *          rounded to float32; uploaded synchronously).
  * Twiddles W_M^k are generated once per device in float64 and rounded to
  * float32.  Errors: INVALID_ARG, UNSUPPORTED_SIZE, INVALID_PLAN, CUDA. */
 int bplg_fft_batched(const void *in, void *out, int64_t n, int64_t batch, int32_t dir,
@@ -224,7 +238,12 @@ int bplg_fft_batched_noalloc(const void *in, void *out, int64_t n, int64_t batch
  *   a,b,c,d device, float32 [batch][n] each (structure of arrays);
  *           a[s][0] and c[s][n-1] are never read.
  *   x       device, float32 [batch][n]; may alias d.
- *   n       power of two, 2 <= n <= 8192; batch >= 1.
+ *   n       2 <= n <= 8192; batch >= 1.  Any n that is not a power of two
+ *           runs the Wang-Mou solver with the plan of the next power of two
+ *           n' (a BPLG_OP_TRIDIAG_WM plan with plan->n == n', or NULL): the
+ *           system is padded with identity rows (a = c = 0, b = 1, d = 0),
+ *           c[s][n-1] is taken as 0, rows stay n apart and nothing past n is
+ *           read or written (element-wise accesses).
  * No pivoting: the systems must be safe for elimination without pivoting
  * (e.g. strictly diagonally dominant).  Errors: as for the scan. */
 int bplg_tridiag_batched(const float *a, const float *b, const float *c, const float *d, float *x,

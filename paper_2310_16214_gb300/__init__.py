@@ -225,7 +225,8 @@ def fft_batched_noalloc(inp, out, n: int, batch: int, direction: int = -1, plan:
 
 
 def tridiag_batched(a, b, c, d, x, n: int, batch: int, plan: Optional[Plan] = None, stream=None) -> None:
-    """CR/PCR tridiagonal solve of [batch][n] float32 systems (see bplg_tridiag_batched)."""
+    """Tridiagonal solve of [batch][n] float32 systems, CR/PCR or Wang-Mou by the plan's op
+    (see bplg_tridiag_batched)."""
     for name, t in (("a", a), ("b", b), ("c", c), ("d", d), ("x", x)):
         _need(name, t, 4 * n * batch)
     _check(lib.bplg_tridiag_batched(_ptr(a), _ptr(b), _ptr(c), _ptr(d), _ptr(x), n, batch, _plan_ref(plan),

@@ -95,12 +95,15 @@ int bplg_scan_batched(int32_t dtype, const void *in, void *out, int64_t n, int64
     if (dtype != BPLG_I32 && dtype != BPLG_F32) return set_error(BPLG_ERR_INVALID_ARG, "scan: dtype must be I32 or F32");
     if (!in || !out) return set_error(BPLG_ERR_INVALID_ARG, "scan: null buffer");
     if (n < 1 || batch < 1) return set_error(BPLG_ERR_INVALID_ARG, "scan: n and batch must be >= 1");
-    if (!size_ok(BPLG_OP_SCAN, n, 1)) return set_error(BPLG_ERR_UNSUPPORTED_SIZE, "scan: n must be a power of two <= 32768");
+    if (n > (int64_t(1) << kScanMaxLog)) return set_error(BPLG_ERR_UNSUPPORTED_SIZE, "scan: n must be <= 32768");
     if (!aligned16(in) || !aligned16(out)) return set_error(BPLG_ERR_INVALID_ARG, "scan: buffers must be 16-byte aligned");
+    // any other n runs the plan of the next power of two, padded with zeros
+    const int64_t np = next_pow2(n);
     bplg_plan p;
     OnlineTicket tk;
-    int rc = resolve_plan(BPLG_OP_SCAN, dtype, n, batch, plan, &p, &tk);
+    int rc = resolve_plan(BPLG_OP_SCAN, dtype, np, batch, plan, &p, np == n ? &tk : nullptr);
     if (rc != BPLG_OK) return rc;
+    p.n = static_cast<int32_t>(np);
     const cudaStream_t s = static_cast<cudaStream_t>(stream);
     if (tk.e0) cudaEventRecord(tk.e0, s);
     rc = scan_launch(p, dtype, in, out, n, batch, s);
@@ -114,8 +117,11 @@ int bplg_fft_batched(const void *in, void *out, int64_t n, int64_t batch, int32_
     if (!in || !out) return set_error(BPLG_ERR_INVALID_ARG, "fft: null buffer");
     if (n < 1 || batch < 1) return set_error(BPLG_ERR_INVALID_ARG, "fft: n and batch must be >= 1");
     if (dir != -1 && dir != 1) return set_error(BPLG_ERR_INVALID_ARG, "fft: dir must be -1 or +1");
-    if (!size_ok(BPLG_OP_FFT, n, 2)) return set_error(BPLG_ERR_UNSUPPORTED_SIZE, "fft: n must be a power of two in [2, 2^24]");
     if (!aligned16(in) || !aligned16(out)) return set_error(BPLG_ERR_INVALID_ARG, "fft: buffers must be 16-byte aligned");
+    if (!is_pow2(n) && n > 2 && n <= (int64_t(1) << kBluesteinMaxLog))
+        return fft_bluestein_launch(plan, in, out, n, batch, dir, static_cast<cudaStream_t>(stream));
+    if (!size_ok(BPLG_OP_FFT, n, 2))
+        return set_error(BPLG_ERR_UNSUPPORTED_SIZE, "fft: n must be in [2, 2^24] (at most 2^23 if not a power of two)");
     bplg_plan p;
     OnlineTicket tk;
     int rc = resolve_plan(BPLG_OP_FFT, BPLG_F32, n, batch, plan, &p, &tk);
@@ -154,15 +160,22 @@ int bplg_tridiag_batched(const float *a, const float *b, const float *c, const f
     clear_error();
     if (!a || !b || !c || !d || !x) return set_error(BPLG_ERR_INVALID_ARG, "tridiag: null buffer");
     if (n < 1 || batch < 1) return set_error(BPLG_ERR_INVALID_ARG, "tridiag: n and batch must be >= 1");
-    if (!size_ok(BPLG_OP_TRIDIAG, n, 2)) return set_error(BPLG_ERR_UNSUPPORTED_SIZE, "tridiag: n must be a power of two in [2, 8192]");
+    if (n < 2 || n > (int64_t(1) << kTridiagMaxLog))
+        return set_error(BPLG_ERR_UNSUPPORTED_SIZE, "tridiag: n must be in [2, 8192]");
     for (const void *q : {(const void *)a, (const void *)b, (const void *)c, (const void *)d, (const void *)x})
         if (!aligned16(q)) return set_error(BPLG_ERR_INVALID_ARG, "tridiag: buffers must be 16-byte aligned");
-    // the plan's op picks the solver: CR/PCR hybrid (default) or Wang-Mou
-    const int op = plan && plan->op == BPLG_OP_TRIDIAG_WM ? BPLG_OP_TRIDIAG_WM : BPLG_OP_TRIDIAG;
+    // the plan's op picks the solver: CR/PCR hybrid (default) or Wang-Mou;
+    // any other n than a power of two runs Wang-Mou on the next power of two
+    const int64_t np = next_pow2(n);
+    if (np != n && plan && plan->op != BPLG_OP_TRIDIAG_WM)
+        return set_error(BPLG_ERR_UNSUPPORTED_SIZE,
+                         "tridiag: n that is not a power of two needs a BPLG_OP_TRIDIAG_WM plan (or NULL)");
+    const int op = np != n || (plan && plan->op == BPLG_OP_TRIDIAG_WM) ? BPLG_OP_TRIDIAG_WM : BPLG_OP_TRIDIAG;
     bplg_plan p;
     OnlineTicket tk;
-    int rc = resolve_plan(op, BPLG_F32, n, batch, plan, &p, &tk);
+    int rc = resolve_plan(op, BPLG_F32, np, batch, plan, &p, np == n ? &tk : nullptr);
     if (rc != BPLG_OK) return rc;
+    p.n = static_cast<int32_t>(np);
     const cudaStream_t s = static_cast<cudaStream_t>(stream);
     if (tk.e0) cudaEventRecord(tk.e0, s);
     rc = op == BPLG_OP_TRIDIAG_WM ? tridiag_wm_launch(p, a, b, c, d, x, n, batch, s)

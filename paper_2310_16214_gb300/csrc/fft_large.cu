@@ -22,13 +22,15 @@
 //   transposed, X[k1 + N1 k2] for row_spb consecutive k1 at a time.
 //
 // y lives in a scratch buffer owned by the library (allocated on first use
-// per device, grown to the largest n x batch seen), so in may equal out.
+// per device and stream, grown to the largest n x batch seen), so in may
+// equal out.
 // W_n^m for n up to 2^24 is a product of two float64-generated tables:
 // W_n^(m mod 4096) (one 4096-entry table per n, cached per device) and
 // W_(n/4096)^(m div 4096) from the main twiddle table.
 #include <algorithm>
 #include <cstring>
 #include <map>
+#include <tuple>
 #include <mutex>
 
 #include "device_util.cuh"
@@ -163,7 +165,8 @@ __global__ void fine_twiddle_kernel(float2 *t, int logn) {
 
 std::mutex g_mu;
 std::map<std::pair<int, int>, float2 *> g_fine;       // (device, log n)
-std::map<int, std::pair<void *, size_t>> g_scratch;  // device -> (buffer, bytes)
+// (device, stream, tag) -> (buffer, bytes)
+std::map<std::tuple<int, cudaStream_t, int>, std::pair<void *, size_t>> g_scratch;
 
 int fine_twiddles(int logn, const float2 **out) {
     int dev = 0;
@@ -197,18 +200,22 @@ int fine_twiddles(int logn, const float2 **out) {
     return BPLG_OK;
 }
 
-// the column results between the two kernels; grows, never shrinks.  A
-// growth synchronises the device first (earlier launches may still use the
-// old buffer), so calls that need no growth never synchronise.
-int scratch(size_t bytes, void **out) {
+}  // namespace
+
+// Library-owned scratch per (device, stream, tag): launches on one stream
+// are ordered, so they may share it, and concurrent streams get their own.
+// It grows, never shrinks; a growth first waits for the stream (earlier
+// launches on it may still use the old buffer), so calls that need no growth
+// never synchronise.
+int stream_scratch(int tag, size_t bytes, cudaStream_t s, void **out) {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return cuda_error(e, "cudaGetDevice");
     std::lock_guard<std::mutex> lock(g_mu);
-    auto &slot = g_scratch[dev];
+    auto &slot = g_scratch[std::make_tuple(dev, s, tag)];
     if (slot.second < bytes) {
         if (slot.first) {
-            e = cudaDeviceSynchronize();
+            e = cudaStreamSynchronize(s);
             if (e != cudaSuccess) return cuda_error(e, "scratch growth");
             cudaFree(slot.first);
             slot = {nullptr, 0};
@@ -221,6 +228,8 @@ int scratch(size_t bytes, void **out) {
     *out = slot.first;
     return BPLG_OK;
 }
+
+namespace {
 
 bool pow2_in(int v, int lo, int hi) { return v >= lo && v <= hi && (v & (v - 1)) == 0; }
 
@@ -314,7 +323,7 @@ int fft_large_launch(const bplg_plan &p, const void *in, void *out, int64_t n, i
     rc = fine_twiddles(logn, &fine);
     if (rc != BPLG_OK) return rc;
     void *y = nullptr;
-    rc = scratch(static_cast<size_t>(n) * static_cast<size_t>(batch) * sizeof(float2), &y);
+    rc = stream_scratch(kScratchLargeFft, static_cast<size_t>(n) * static_cast<size_t>(batch) * sizeof(float2), s, &y);
     if (rc != BPLG_OK) return rc;
     rc = ensure_smem_attr(l0.func, l0.smem);
     if (rc == BPLG_OK) rc = ensure_smem_attr(l1.func, l1.smem);

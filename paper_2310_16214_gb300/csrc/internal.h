@@ -25,6 +25,11 @@ inline int ilog2(int64_t v) {
     return l;
 }
 inline bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+inline int64_t next_pow2(int64_t v) {
+    int64_t p = 1;
+    while (p < v) p <<= 1;
+    return p;
+}
 
 // Kernel function pointer plus the launch geometry derived from a plan.
 struct Launch {
@@ -104,6 +109,18 @@ void bo_destroy(BoSearch *b);
 bool cache_lookup(int op, int dtype, int64_t n, int64_t batch, bplg_plan *out);
 void cache_store(int op, int dtype, int64_t n, int64_t batch, const bplg_plan &p);
 int analytic_plan(int op, int dtype, int64_t n, bplg_plan *out);
+
+// library-owned device scratch per (device, stream, tag) (fft_large.cu)
+constexpr int kScratchLargeFft = 0;
+constexpr int kScratchBluestein = 1;
+int stream_scratch(int tag, size_t bytes, cudaStream_t s, void **out);
+
+// FFT of a length that is not a power of two (fft_bluestein.cu): Bluestein's
+// chirp identity over power-of-two FFTs of size M >= 2n - 1 (plan: one for M,
+// or NULL)
+constexpr int kBluesteinMaxLog = 23;
+int fft_bluestein_launch(const bplg_plan *plan_m, const void *in, void *out, int64_t n, int64_t batch, int dir,
+                         cudaStream_t s);
 
 // twiddle table of the current device (float2 W_M^k at [M + k], M = 2..2^14)
 int twiddles_for_current_device(const void **tw);

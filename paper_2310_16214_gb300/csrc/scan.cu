@@ -12,12 +12,18 @@
 //   3. when T > 32, one shared-memory slot per warp (the 32-slots-per-problem
 //      scheme of Section V-B) and a second shuffle prefix over the warp totals.
 // int32 arithmetic wraps modulo 2^32, which is exactly the definition.
+//
+// Problems of any length n (not only powers of two, the identity padding of
+// a non-power-of-two size): the kernel of the next power of two n' runs with
+// RAGGED set; rows are n apart, elements n..n'-1 read as 0 (the identity of
+// the sum) and are not written.  Those loads are element-wise (rows are not
+// 16-byte aligned in general).
 #include "device_util.cuh"
 #include "internal.h"
 
 namespace bplg {
 
-template <typename E, int P, int PATTERN>
+template <typename E, int P, int PATTERN, bool RAGGED>
 __global__ void __launch_bounds__(1024)
     scan_kernel(const E *in, E *out, int log_t, int spb, int64_t batch, int64_t n) {
     __shared__ E warp_tot[32];
@@ -30,7 +36,10 @@ __global__ void __launch_bounds__(1024)
     const int64_t base = sig * n + static_cast<int64_t>(t) * P;
 
     E v[P];
-    if (active) {
+    if constexpr (RAGGED) {
+#pragma unroll
+        for (int i = 0; i < P; ++i) v[i] = (active && t * P + i < n) ? in[base + i] : E(0);
+    } else if (active) {
         load_run<E, P>(in + base, v);
     } else {
 #pragma unroll
@@ -60,33 +69,39 @@ __global__ void __launch_bounds__(1024)
     }
 #pragma unroll
     for (int i = 0; i < P; ++i) v[i] += excl;
-    if (active) store_run<E, P>(out + base, v);
+    if constexpr (RAGGED) {
+#pragma unroll
+        for (int i = 0; i < P; ++i)
+            if (active && t * P + i < n) out[base + i] = v[i];
+    } else if (active) {
+        store_run<E, P>(out + base, v);
+    }
 }
 
 namespace {
 
-template <typename E, int P>
+template <typename E, int P, bool RAGGED>
 const void *scan_func_p(int pattern) {
-    return pattern == BPLG_PATTERN_LF ? reinterpret_cast<const void *>(&scan_kernel<E, P, 1>)
-                                      : reinterpret_cast<const void *>(&scan_kernel<E, P, 0>);
+    return pattern == BPLG_PATTERN_LF ? reinterpret_cast<const void *>(&scan_kernel<E, P, 1, RAGGED>)
+                                      : reinterpret_cast<const void *>(&scan_kernel<E, P, 0, RAGGED>);
 }
 
-template <typename E>
+template <typename E, bool RAGGED>
 const void *scan_func_t(int P, int pattern) {
     switch (P) {
-        case 1: return scan_func_p<E, 1>(pattern);
-        case 2: return scan_func_p<E, 2>(pattern);
-        case 4: return scan_func_p<E, 4>(pattern);
-        case 8: return scan_func_p<E, 8>(pattern);
-        case 16: return scan_func_p<E, 16>(pattern);
-        case 32: return scan_func_p<E, 32>(pattern);
+        case 1: return scan_func_p<E, 1, RAGGED>(pattern);
+        case 2: return scan_func_p<E, 2, RAGGED>(pattern);
+        case 4: return scan_func_p<E, 4, RAGGED>(pattern);
+        case 8: return scan_func_p<E, 8, RAGGED>(pattern);
+        case 16: return scan_func_p<E, 16, RAGGED>(pattern);
+        case 32: return scan_func_p<E, 32, RAGGED>(pattern);
         default: return nullptr;
     }
 }
 
-const void *scan_func(int dtype, int P, int pattern) {
-    if (dtype == BPLG_I32) return scan_func_t<int32_t>(P, pattern);
-    if (dtype == BPLG_F32) return scan_func_t<float>(P, pattern);
+const void *scan_func(int dtype, int P, int pattern, bool ragged) {
+    if (dtype == BPLG_I32) return ragged ? scan_func_t<int32_t, true>(P, pattern) : scan_func_t<int32_t, false>(P, pattern);
+    if (dtype == BPLG_F32) return ragged ? scan_func_t<float, true>(P, pattern) : scan_func_t<float, false>(P, pattern);
     return nullptr;
 }
 
@@ -95,7 +110,7 @@ const void *scan_func(int dtype, int P, int pattern) {
 bool scan_launch_info(const bplg_plan &p, int dtype, int64_t n, int64_t batch, Launch *out) {
     std::string why;
     if (!plan_structurally_valid(p, dtype, n, &why)) return false;
-    const void *f = scan_func(dtype, p.P, p.pattern);
+    const void *f = scan_func(dtype, p.P, p.pattern, false);
     if (!f) return false;
     out->func = f;
     out->threads = p.L;
@@ -106,9 +121,13 @@ bool scan_launch_info(const bplg_plan &p, int dtype, int64_t n, int64_t batch, L
 
 int scan_launch(const bplg_plan &p, int dtype, const void *in, void *out, int64_t n, int64_t batch,
                 cudaStream_t s) {
+    // a plan made for the next power of two runs a length-n problem padded
+    const int64_t np = p.n > 0 ? p.n : n;
+    if (np < n || (np != n && np / 2 >= n)) return set_error(BPLG_ERR_INVALID_PLAN, "scan: plan is for another n");
     Launch li;
-    if (!scan_launch_info(p, dtype, n, batch, &li)) return set_error(BPLG_ERR_INVALID_PLAN, "scan: plan has no kernel");
-    int log_t = ilog2(n / p.P);
+    if (!scan_launch_info(p, dtype, np, batch, &li)) return set_error(BPLG_ERR_INVALID_PLAN, "scan: plan has no kernel");
+    if (np != n) li.func = scan_func(dtype, p.P, p.pattern, true);
+    int log_t = ilog2(np / p.P);
     int spb = p.spb;
     void *args[] = {const_cast<void **>(&in), &out, &log_t, &spb, &batch, &n};
     cudaError_t e = cudaLaunchKernel(li.func, dim3(static_cast<unsigned>(li.blocks)), dim3(li.threads), args,

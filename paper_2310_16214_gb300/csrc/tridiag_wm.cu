@@ -52,46 +52,66 @@ namespace {
 
 using wm::wm_warp_only;
 
-template <int P, int R, int SHUFFLE, int MAXT>
+// RAGGED: systems of nrow < 2^logn equations (rows nrow apart), solved as
+// the power-of-two system padded with identity rows (a = c = 0, b = 1,
+// d = 0, whose unknowns are 0); c of the last real row is taken as 0 and
+// nothing past nrow is read or written.  Element-wise accesses there.
+template <int P, int R, int SHUFFLE, int MAXT, bool RAGGED>
 __global__ void __launch_bounds__(MAXT)
     tridiag_wm_kernel(const float *ga, const float *gb, const float *gc, const float *gd, float *x, int logn,
-                      int log_tps, int spb, int64_t batch) {
+                      int log_tps, int spb, int64_t batch, int nrow) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int n = 1 << logn;
     const int s = threadIdx.x >> log_tps;
     const int t = threadIdx.x & ((1 << log_tps) - 1);
     const int64_t sig0 = static_cast<int64_t>(blockIdx.x) * spb;
     const int64_t left = batch - sig0;
     const int nvalid = left < spb ? static_cast<int>(left) : spb;
     const bool active = s < nvalid;
-    const int64_t g0 = (sig0 + s) * n + static_cast<int64_t>(t) * P;
-    wm::wm_solve<P, R, SHUFFLE>(ga + g0, gb + g0, gc + g0, gd + g0, x + g0, active, log_tps,
-                                reinterpret_cast<float4 *>(smem_raw));
+    float4 *buf = reinterpret_cast<float4 *>(smem_raw);
+    if constexpr (!RAGGED) {
+        const int64_t g0 = (sig0 + s) * (int64_t(1) << logn) + static_cast<int64_t>(t) * P;
+        wm::wm_solve<P, R, SHUFFLE>(ga + g0, gb + g0, gc + g0, gd + g0, x + g0, active, log_tps, buf);
+    } else {
+        const int i0 = t * P;
+        const int64_t g0 = (sig0 + s) * static_cast<int64_t>(nrow) + i0;
+        float a[P], b[P], c[P], d[P];
+#pragma unroll
+        for (int i = 0; i < P; ++i) {
+            const bool in = active && i0 + i < nrow;
+            a[i] = in ? ga[g0 + i] : 0.f;
+            b[i] = in ? gb[g0 + i] : 1.f;
+            c[i] = active && i0 + i < nrow - 1 ? gc[g0 + i] : 0.f;
+            d[i] = in ? gd[g0 + i] : 0.f;
+        }
+        const int nval = nrow - i0 < 0 ? 0 : (nrow - i0 < P ? nrow - i0 : P);
+        wm::wm_solve_regs<P, R, SHUFFLE>(a, b, c, d, x + g0, active && nval > 0, log_tps, buf, nval);
+    }
 }
 
-template <int P, int R>
+template <int P, int R, bool RAGGED>
 const void *wm_func_r(int shuffle) {
     constexpr int MAXT = P >= 8 || R >= 8 ? 512 : 1024;
-    return shuffle ? reinterpret_cast<const void *>(&tridiag_wm_kernel<P, R, 1, MAXT>)
-                   : reinterpret_cast<const void *>(&tridiag_wm_kernel<P, R, 0, MAXT>);
+    return shuffle ? reinterpret_cast<const void *>(&tridiag_wm_kernel<P, R, 1, MAXT, RAGGED>)
+                   : reinterpret_cast<const void *>(&tridiag_wm_kernel<P, R, 0, MAXT, RAGGED>);
 }
 
-template <int P>
+template <int P, bool RAGGED>
 const void *wm_func_p(int radix, int shuffle) {
     switch (radix) {
-        case 2: return wm_func_r<P, 2>(shuffle);
-        case 4: return wm_func_r<P, 4>(shuffle);
-        case 8: return wm_func_r<P, 8>(shuffle);
+        case 2: return wm_func_r<P, 2, RAGGED>(shuffle);
+        case 4: return wm_func_r<P, 4, RAGGED>(shuffle);
+        case 8: return wm_func_r<P, 8, RAGGED>(shuffle);
         default: return nullptr;
     }
 }
 
+template <bool RAGGED>
 const void *wm_func(int P, int radix, int shuffle) {
     switch (P) {
-        case 2: return wm_func_p<2>(radix, shuffle);
-        case 4: return wm_func_p<4>(radix, shuffle);
-        case 8: return wm_func_p<8>(radix, shuffle);
-        case 16: return wm_func_p<16>(radix, shuffle);
+        case 2: return wm_func_p<2, RAGGED>(radix, shuffle);
+        case 4: return wm_func_p<4, RAGGED>(radix, shuffle);
+        case 8: return wm_func_p<8, RAGGED>(radix, shuffle);
+        case 16: return wm_func_p<16, RAGGED>(radix, shuffle);
         default: return nullptr;
     }
 }
@@ -105,7 +125,7 @@ int tridiag_wm_smem_bytes(const bplg_plan &p, int64_t n) {
 
 bool tridiag_wm_launch_info(const bplg_plan &p, int64_t n, int64_t batch, Launch *out) {
     if (!plan_structurally_valid(p, BPLG_F32, n, nullptr)) return false;
-    const void *f = wm_func(p.P, p.radix, p.shuffle);
+    const void *f = wm_func<false>(p.P, p.radix, p.shuffle);
     if (!f) return false;
     out->func = f;
     out->threads = p.L;
@@ -116,13 +136,17 @@ bool tridiag_wm_launch_info(const bplg_plan &p, int64_t n, int64_t batch, Launch
 
 int tridiag_wm_launch(const bplg_plan &p, const float *a, const float *b, const float *c, const float *d, float *x,
                       int64_t n, int64_t batch, cudaStream_t s) {
+    // a plan made for the next power of two runs a length-n system padded
+    const int64_t np = p.n > 0 ? p.n : n;
+    if (np < n || (np != n && np / 2 >= n)) return set_error(BPLG_ERR_INVALID_PLAN, "tridiag (Wang-Mou): plan is for another n");
     Launch li;
-    if (!tridiag_wm_launch_info(p, n, batch, &li))
+    if (!tridiag_wm_launch_info(p, np, batch, &li))
         return set_error(BPLG_ERR_INVALID_PLAN, "tridiag (Wang-Mou): plan has no kernel");
+    if (np != n) li.func = wm_func<true>(p.P, p.radix, p.shuffle);
     int rc = ensure_smem_attr(li.func, li.smem);
     if (rc != BPLG_OK) return rc;
-    int logn = ilog2(n), log_tps = ilog2(n / p.P), spb = p.spb;
-    void *args[] = {(void *)&a, (void *)&b, (void *)&c, (void *)&d, (void *)&x, &logn, &log_tps, &spb, &batch};
+    int logn = ilog2(np), log_tps = ilog2(np / p.P), spb = p.spb, nrow = static_cast<int>(n);
+    void *args[] = {(void *)&a, (void *)&b, (void *)&c, (void *)&d, (void *)&x, &logn, &log_tps, &spb, &batch, &nrow};
     cudaError_t e = cudaLaunchKernel(li.func, dim3(static_cast<unsigned>(li.blocks)), dim3(li.threads), args,
                                      static_cast<size_t>(li.smem), s);
     return e == cudaSuccess ? BPLG_OK

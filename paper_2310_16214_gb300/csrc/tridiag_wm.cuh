@@ -114,12 +114,13 @@ __host__ __device__ __forceinline__ bool wm_warp_only(int shuffle, int64_t tps) 
 // One system (or, with several systems per block, each of them) solved by
 // the threads that serve it, from this thread's P equations in registers
 // (identity rows where `active` is false; a..d are destroyed).  x points at
-// the thread's P unknowns.  buf is the block's shared memory (4 float4 per
-// thread) unless every exchange is a warp shuffle.  Every thread of the
-// block calls it.
+// the thread's P unknowns, of which the first `nval` are written (fewer
+// than P only in the last run of a padded system).  buf is the block's
+// shared memory (4 float4 per thread) unless every exchange is a warp
+// shuffle.  Every thread of the block calls it.
 template <int P, int R, int SHUFFLE>
 __device__ __forceinline__ void wm_solve_regs(float (&a)[P], float (&b)[P], float (&c)[P], float (&d)[P], float *x,
-                                              bool active, int log_tps, float4 *buf) {
+                                              bool active, int log_tps, float4 *buf, int nval = P) {
     const int tps = 1 << log_tps;
     const int tid = threadIdx.x;
     const int t = tid & (tps - 1);
@@ -191,7 +192,15 @@ __device__ __forceinline__ void wm_solve_regs(float (&a)[P], float (&b)[P], floa
     float xv[P];
 #pragma unroll
     for (int i = 0; i < P; ++i) xv[i] = fmaf(gm[i], xr_nb, fmaf(be[i], xl_nb, al[i]));
-    if (active) store_run<float, P>(x, xv);
+    if (active) {
+        if (nval >= P) {
+            store_run<float, P>(x, xv);
+        } else {
+#pragma unroll
+            for (int i = 0; i < P; ++i)
+                if (i < nval) x[i] = xv[i];
+        }
+    }
 }
 
 // The same reading the thread's P equations from global memory (ga..gd).

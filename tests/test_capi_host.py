@@ -216,11 +216,13 @@ def test_argument_errors_before_any_device_call():
     P = bp.lib
     assert P.bplg_scan_batched(0, None, None, 64, 1, None, None) == bp.ERR_INVALID_ARG
     assert P.bplg_scan_batched(7, 16, 16, 64, 1, None, None) == bp.ERR_INVALID_ARG
-    assert P.bplg_scan_batched(0, 16, 16, 63, 1, None, None) == bp.ERR_UNSUPPORTED_SIZE
+    assert P.bplg_scan_batched(0, 16, 16, 32769, 1, None, None) == bp.ERR_UNSUPPORTED_SIZE  # above 2^15
     assert P.bplg_scan_batched(0, 16, 16, 64, 0, None, None) == bp.ERR_INVALID_ARG
     assert P.bplg_scan_batched(0, 17, 16, 64, 1, None, None) == bp.ERR_INVALID_ARG  # misaligned
     assert P.bplg_fft_batched(16, 16, 64, 1, 0, None, None) == bp.ERR_INVALID_ARG
     assert P.bplg_fft_batched(16, 16, 1 << 25, 1, -1, None, None) == bp.ERR_UNSUPPORTED_SIZE
+    assert P.bplg_fft_batched(16, 16, (1 << 23) + 1, 1, -1, None, None) == bp.ERR_UNSUPPORTED_SIZE  # Bluestein limit
+    assert P.bplg_tridiag_batched(16, 16, 16, 16, 16, 1, 1, None, None) == bp.ERR_UNSUPPORTED_SIZE
     assert P.bplg_tridiag_batched(16, 16, 16, None, 16, 64, 1, None, None) == bp.ERR_INVALID_ARG
     assert P.bplg_tridiag_batched(16, 16, 16, 16, 16, 1 << 14, 1, None, None) == bp.ERR_UNSUPPORTED_SIZE
     assert P.bplg_tridiag_refined(16, 16, 16, 16, 4096, 64, 1, 65, 1e-14, None, None, None) == bp.ERR_INVALID_ARG

@@ -238,3 +238,40 @@ def test_phi_closed_form():
     assert abs(T.phi([1.0, 0.5]) - 2.0 / 3.0) < 1e-15
     assert abs(T.phi([0.9] * 7) - 0.9) < 1e-15
     assert T.phi([]) == 0.0
+
+
+# ------------------------------------------- lengths that are not powers of two
+
+@pytest.mark.parametrize("n", [3, 5, 6, 7, 12, 100, 243, 1000])
+def test_dft_any_length_vs_numpy(n):
+    # the O(N^2) oracle is the reference for the Bluestein path: it must hold
+    # for every length, not only powers of two
+    x = si.fft_c64(2, n, stream=n).astype(np.complex128)
+    ref = np.fft.fft(x, axis=-1)
+    scale = np.linalg.norm(ref)
+    assert np.linalg.norm(oracle.dft(x, -1) - ref) / scale < 1e-13
+    assert np.linalg.norm(oracle.dft(x, +1) - n * np.fft.ifft(x, axis=-1)) / scale < 1e-13
+
+
+@pytest.mark.parametrize("n", [3, 35, 1000])
+def test_dft_any_length_closed_forms(n):
+    k = np.arange(n)
+    j0, f = min(2, n - 1), min(4, n - 1)
+    imp = np.zeros((1, n), np.complex128)
+    imp[0, j0] = 1
+    assert np.allclose(oracle.dft(imp, -1)[0], np.exp(-2j * np.pi * j0 * k / n), atol=1e-13)
+    tone = np.exp(2j * np.pi * f * k / n)[None, :]
+    spike = np.zeros(n, np.complex128)
+    spike[f] = n
+    assert np.allclose(oracle.dft(tone, -1)[0], spike, atol=1e-9 * n)
+
+
+@pytest.mark.parametrize("n", [1, 3, 33, 1000])
+def test_scan_and_thomas_any_length(n):
+    x = si.scan_i32(3, n, stream=n)
+    ref = (np.cumsum(x.astype(np.int64), axis=1) & 0xFFFFFFFF).astype(np.uint32).view(np.int32)
+    assert np.array_equal(oracle.scan_i32(x), ref)
+    if n >= 2:
+        a, b, c, d, xt = si.tridiag_f32(2, n, stream=n)
+        A = np.diag(b[0].astype(np.float64)) + np.diag(a[0, 1:].astype(np.float64), -1) + np.diag(c[0, :-1].astype(np.float64), 1)
+        assert np.allclose(oracle.thomas(a, b, c, d)[0], np.linalg.solve(A, d[0].astype(np.float64)), rtol=1e-12, atol=1e-13)
