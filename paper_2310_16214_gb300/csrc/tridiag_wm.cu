@@ -84,7 +84,7 @@ __global__ void __launch_bounds__(MAXT)
             d[i] = in ? gd[g0 + i] : 0.f;
         }
         const int nval = nrow - i0 < 0 ? 0 : (nrow - i0 < P ? nrow - i0 : P);
-        wm::wm_solve_regs<P, R, SHUFFLE>(a, b, c, d, x + g0, active && nval > 0, log_tps, buf, nval);
+        wm::wm_solve_regs<P, R, SHUFFLE>(a, b, c, d, x + g0, active && nval > 0, log_tps, buf, nval, false);
     }
 }
 

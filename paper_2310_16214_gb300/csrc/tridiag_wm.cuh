@@ -115,12 +115,15 @@ __host__ __device__ __forceinline__ bool wm_warp_only(int shuffle, int64_t tps) 
 // the threads that serve it, from this thread's P equations in registers
 // (identity rows where `active` is false; a..d are destroyed).  x points at
 // the thread's P unknowns, of which the first `nval` are written (fewer
-// than P only in the last run of a padded system).  buf is the block's
+// than P only in the last run of a padded system); with `vec` false every
+// store is element-wise (rows of a padded system need not be 16-byte
+// aligned).  buf is the block's
 // shared memory (4 float4 per thread) unless every exchange is a warp
 // shuffle.  Every thread of the block calls it.
 template <int P, int R, int SHUFFLE>
 __device__ __forceinline__ void wm_solve_regs(float (&a)[P], float (&b)[P], float (&c)[P], float (&d)[P], float *x,
-                                              bool active, int log_tps, float4 *buf, int nval = P) {
+                                              bool active, int log_tps, float4 *buf, int nval = P,
+                                              bool vec = true) {
     const int tps = 1 << log_tps;
     const int tid = threadIdx.x;
     const int t = tid & (tps - 1);
@@ -193,7 +196,7 @@ __device__ __forceinline__ void wm_solve_regs(float (&a)[P], float (&b)[P], floa
 #pragma unroll
     for (int i = 0; i < P; ++i) xv[i] = fmaf(gm[i], xr_nb, fmaf(be[i], xl_nb, al[i]));
     if (active) {
-        if (nval >= P) {
+        if (vec && nval >= P) {
             store_run<float, P>(x, xv);
         } else {
 #pragma unroll

@@ -87,7 +87,7 @@ def test_argument_errors(bp):
     z = torch.zeros(2 * 64, dtype=torch.float32, device="cuda")
     # sizes the library rejects before any launch (raw pointers: the binding's
     # tensor-size check is not involved)
-    for n in (3, 1 << 25):
+    for n in ((1 << 23) + 1, 1 << 25):  # above the Bluestein limit / above 2^24
         assert bp.lib.bplg_fft_batched(z.data_ptr(), z.data_ptr(), n, 1, -1, None, None) == bp.ERR_UNSUPPORTED_SIZE
     # a tensor too small for n x batch is refused by the binding
     with pytest.raises(ValueError):

@@ -91,9 +91,10 @@ def test_default_plan_full_size_sampled(bp):
 
 def test_argument_errors(bp):
     x = torch.zeros(64, dtype=torch.int32, device="cuda")
-    with pytest.raises(bp.BplgError) as e:
-        bp.scan_batched(x, x, 3, 1)
-    assert e.value.code == bp.ERR_UNSUPPORTED_SIZE
+    # above 2^15 the library refuses before any launch (raw pointers: the
+    # binding's tensor-size check is not involved); every smaller n is valid
+    assert bp.lib.bplg_scan_batched(bp.I32, x.data_ptr(), x.data_ptr(), (1 << 15) + 1, 1, None, None) == \
+        bp.ERR_UNSUPPORTED_SIZE
     with pytest.raises(bp.BplgError) as e:
         bp.scan_batched(x.data_ptr() + 4, x, 16, 1, dtype=bp.I32)
     assert e.value.code == bp.ERR_INVALID_ARG

@@ -145,9 +145,9 @@ def test_refined_zero_iterations_is_the_float32_solve(bp):
 
 def test_argument_errors(bp):
     v = torch.zeros(8192, dtype=torch.float32, device="cuda")
-    with pytest.raises(bp.BplgError) as e:
-        bp.tridiag_batched(v, v, v, v, v, 100, 1)
-    assert e.value.code == bp.ERR_UNSUPPORTED_SIZE
+    # n outside [2, 8192] is refused before any launch (raw pointers)
+    for n in (1, 8193):
+        assert bp.lib.bplg_tridiag_batched(*([v.data_ptr()] * 5), n, 1, None, None) == bp.ERR_UNSUPPORTED_SIZE
     x64 = torch.zeros(8192, dtype=torch.float64, device="cuda")
     with pytest.raises(bp.BplgError) as e:
         bp.tridiag_refined(v, v, v, v, v, 64, 1)  # x aliases the inputs
