@@ -930,6 +930,73 @@ def largefft_report(args):
     return rows
 
 
+def nonpow2_report(args):
+    """Lengths that are not powers of two, 2^24 elements per case: the padded
+    scan (int32) and Wang-Mou solve on the next power of two against the
+    power-of-two length just below, and Bluestein FFTs against cuFFT (which
+    runs such lengths with its own mixed-radix or Bluestein kernels).  Every
+    row reports the time, Gelem/s and the fraction of the measured copy
+    bandwidth for the algorithmic bytes (scan 8, tridiag 20, FFT 16 per
+    element)."""
+    import ctypes
+    import torch
+    torch.cuda.set_device(0)
+    import paper_2310_16214_gb300 as bp
+    peak, _ = read_peaks()
+    st = torch.cuda.current_stream()
+    lib = ctypes.CDLL(os.path.join(ROOT, "paper_2310_16214_gb300", "_lib", "libbplg_extref.so"))
+    lib.extref_fft_c2c.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64, ctypes.c_int,
+                                   ctypes.c_void_p]
+
+    def timeit(fn):
+        for _ in range(3):
+            fn()
+        evs = []
+        for _ in range(args.reps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(st)
+            fn()
+            e1.record(st)
+            evs.append((e0, e1))
+        torch.cuda.synchronize()
+        return statistics.median(a.elapsed_time(b) for a, b in evs)
+
+    def line(kind, n, batch, ms, bpe, extra=None):
+        row = {"op": kind, "n": n, "batch": batch, "ms": round(ms, 5),
+               "gelem_s": round(n * batch / (ms * 1e-3) / 1e9, 1),
+               "hbm_frac": round(bpe * n * batch / (ms * 1e-3) / 1e9 / peak, 4)}
+        row.update(extra or {})
+        print(json.dumps(row), flush=True)
+        return row
+
+    rows = []
+    total = 1 << 24
+    for n in (1000, 1024, 5000, 4096):
+        batch = total // n
+        x = torch.randint(-1000, 1000, (n * batch,), dtype=torch.int32, device="cuda")
+        y = torch.empty_like(x)
+        rows.append(line("scan_i32", n, batch, timeit(lambda: bp.scan_batched(x, y, n, batch, dtype=bp.I32)), 8))
+    for n in (1000, 1024, 3000, 2048):
+        batch = total // n
+        a, b, c, d, _ = si.tridiag_f32(batch, n, stream=950 + n)
+        ts = [torch.from_numpy(v.reshape(-1)).cuda() for v in (a, b, c, d)]
+        xo = torch.empty_like(ts[0])
+        p = bp.query_plan(bp.OP_TRIDIAG_WM, bp.F32, 1 << (n - 1).bit_length(), batch)
+        rows.append(line("tridiag_wm", n, batch, timeit(lambda: bp.tridiag_batched(*ts, xo, n, batch, plan=p)), 20,
+                         {"plan_n": p.n}))
+    for n in (1000, 3000, 100003):
+        batch = max(1, total // n)
+        z = torch.rand(2 * n * batch, device="cuda") * 2 - 1
+        zo = torch.empty_like(z)
+        ms = timeit(lambda: bp.fft_batched(z, zo, n, batch, -1))
+        tc = timeit(lambda: lib.extref_fft_c2c(ctypes.c_void_p(z.data_ptr()), ctypes.c_void_p(zo.data_ptr()), n, batch,
+                                               -1, ctypes.c_void_p(st.cuda_stream)))
+        M = 1 << (2 * n - 2).bit_length()
+        rows.append(line("fft_bluestein", n, batch, ms, 16, {"inner_M": M, "cufft_ms": round(tc, 5),
+                                                             "ours_speedup_vs_cufft": round(tc / ms, 3)}))
+    return rows
+
+
 def precision_report(args):
     """Precision configuration: FFT N in {2^10, 2^12, 2^14}, batch 2^26/N,
     tensor-core radix-16 stages with BF16 and FP16 split operands against
@@ -997,6 +1064,8 @@ def main():
     ap.add_argument("--tune-report", action="store_true", help="tuned vs exhaustive Phi report instead of the bench")
     ap.add_argument("--precision-report", action="store_true",
                     help="tensor-core (BF16/FP16 split) vs float32 FFT: error and time per N")
+    ap.add_argument("--nonpow2-report", action="store_true",
+                    help="scan / Wang-Mou / Bluestein FFT at lengths that are not powers of two")
     ap.add_argument("--largefft-report", action="store_true",
                     help="FFTs above 16384 points: tuners vs exhaustive (Phi) and cuFFT")
     ap.add_argument("--uneven-report", action="store_true",
@@ -1017,6 +1086,8 @@ def main():
         precision_report(args)
     elif args.uneven_report:
         uneven_report(args)
+    elif args.nonpow2_report:
+        nonpow2_report(args)
     elif args.largefft_report:
         largefft_report(args)
     elif args.impl == "reference":

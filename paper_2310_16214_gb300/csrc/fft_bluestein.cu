@@ -15,20 +15,81 @@
 // accuracy for large m.  G is computed once on the host in float64 (an
 // iterative radix-2 FFT) and rounded to float32, like the twiddle tables;
 // the data never leaves the GPU.
+//
+// For 32 <= M <= 8192 (and no caller plan) the whole chain is one kernel,
+// one signal per M/16 threads: the chirp product is formed as the signal is
+// loaded, the forward M-point transform (the compile-time radix-16 stage
+// schedule) writes its output times G into the shared-memory exchange
+// buffer, the inverse transform reads it back and its last stage writes
+// h_k c_k for k < n straight to global memory.  HBM then carries 16 bytes
+// per element, as for a power-of-two length.  Otherwise (or with a plan for
+// the M-point transforms) the chain runs as three elementwise kernels and
+// two batched FFT launches through a scratch buffer.
 #include <cmath>
 #include <map>
 #include <mutex>
 #include <tuple>
 #include <vector>
 
+#include "fft_common.cuh"
 #include "internal.h"
 
 namespace bplg {
 
 namespace {
 
-__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
-    return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
+constexpr int kFusedMinLog = 5, kFusedMaxLog = 13;  // at most 512 threads: 128 registers each
+
+// The fused chain for M = 2^LOGM (radix 16, padded interleaved exchange).
+template <int LOGM>
+__global__ void __launch_bounds__(512)
+    bluestein_fused_kernel(const float2 *__restrict__ x, float2 *__restrict__ X, const float2 *__restrict__ h,
+                           const float2 *__restrict__ G, const float2 *__restrict__ tw, int64_t n, int spb,
+                           int64_t batch) {
+    using S = FftShape<16, LOGM>;
+    constexpr int M = 1 << LOGM;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int tid = threadIdx.x;
+    const int s = tid >> S::LOGT;
+    const int j = tid & (S::T - 1);
+    const int64_t sig = static_cast<int64_t>(blockIdx.x) * spb + s;
+    const bool active = sig < batch;
+    float2 *buf2 = reinterpret_cast<float2 *>(smem_raw) + s * sig_stride<0, 1>(M);
+    float *buf1 = reinterpret_cast<float *>(buf2);
+    const float2 *xs = x + sig * n;
+    float2 v[16];
+#pragma unroll
+    for (int m = 0; m < 16; ++m) {
+        const int e = j + m * S::T;
+        v[m] = active && e < n ? cmul(__ldcs(xs + e), __ldg(h + e)) : make_float2(0.f, 0.f);
+    }
+    // forward transform; its output times G goes to the exchange buffer
+    auto to_smem = [&](int pos, float2 val) { buf2[pad_g<16>(pos)] = cmul(val, __ldg(G + pos)); };
+    fft_fixed_stages_st<16, LOGM, -1, 0, 0, true>(v, buf2, buf1, j, tw, to_smem);
+    __syncthreads();
+#pragma unroll
+    for (int m = 0; m < 16; ++m) v[m] = buf2[pad_g<16>(j + m * S::T)];
+    // inverse transform; X_k = h_k c_k for k < n
+    float2 *Xs = X + sig * n;
+    auto to_out = [&](int pos, float2 val) {
+        if (active && pos < n) __stcs(Xs + pos, cmul(val, __ldg(h + pos)));
+    };
+    fft_fixed_stages_st<16, LOGM, 1, 0, 0, true>(v, buf2, buf1, j, tw, to_out);
+}
+
+const void *fused_func(int logm) {
+    switch (logm) {
+        case 5: return reinterpret_cast<const void *>(&bluestein_fused_kernel<5>);
+        case 6: return reinterpret_cast<const void *>(&bluestein_fused_kernel<6>);
+        case 7: return reinterpret_cast<const void *>(&bluestein_fused_kernel<7>);
+        case 8: return reinterpret_cast<const void *>(&bluestein_fused_kernel<8>);
+        case 9: return reinterpret_cast<const void *>(&bluestein_fused_kernel<9>);
+        case 10: return reinterpret_cast<const void *>(&bluestein_fused_kernel<10>);
+        case 11: return reinterpret_cast<const void *>(&bluestein_fused_kernel<11>);
+        case 12: return reinterpret_cast<const void *>(&bluestein_fused_kernel<12>);
+        case 13: return reinterpret_cast<const void *>(&bluestein_fused_kernel<13>);
+        default: return nullptr;
+    }
 }
 
 // a[s][j] = x[s][j] h_j for j < n, 0 for n <= j < M
@@ -169,6 +230,24 @@ int fft_bluestein_launch(const bplg_plan *plan_m, const void *in, void *out, int
     Tables t;
     int rc = tables_for(n, dir, logm, &t);
     if (rc != BPLG_OK) return rc;
+    if (!plan_m && logm >= kFusedMinLog && logm <= kFusedMaxLog) {
+        const void *tw = nullptr;
+        rc = twiddles_for_current_device(&tw);
+        if (rc != BPLG_OK) return rc;
+        const void *f = fused_func(logm);
+        const int T = static_cast<int>(M / 16);
+        int spb = T >= 256 ? 1 : 256 / T;  // 256 or 512 threads per block
+        const int smem = spb * sig_stride<0, 1>(static_cast<int>(M)) * static_cast<int>(sizeof(float2));
+        rc = ensure_smem_attr(f, smem);
+        if (rc != BPLG_OK) return rc;
+        const int64_t blocks = (batch + spb - 1) / spb;
+        const float2 *xi = static_cast<const float2 *>(in);
+        float2 *xo = static_cast<float2 *>(out);
+        void *args[] = {(void *)&xi, (void *)&xo, (void *)&t.h, (void *)&t.G, (void *)&tw, &n, &spb, &batch};
+        cudaError_t e = cudaLaunchKernel(f, dim3(static_cast<unsigned>(blocks)), dim3(T * spb), args,
+                                         static_cast<size_t>(smem), s);
+        return e == cudaSuccess ? BPLG_OK : launch_error(e, "Bluestein fused launch", f, blocks, T * spb, smem);
+    }
     // the inner transforms' plan: the caller's (made for M) or the default
     bplg_plan pm;
     if (plan_m) {

@@ -16,8 +16,10 @@
 // Problems of any length n (not only powers of two, the identity padding of
 // a non-power-of-two size): the kernel of the next power of two n' runs with
 // RAGGED set; rows are n apart, elements n..n'-1 read as 0 (the identity of
-// the sum) and are not written.  Those loads are element-wise (rows are not
-// 16-byte aligned in general).
+// the sum) and are not written.  When n is a multiple of 4 every row starts
+// on a 16-byte boundary and a 4-element group is either wholly inside the
+// row or wholly past it, so the accesses stay 16 bytes wide; otherwise they
+// are element-wise.
 #include "device_util.cuh"
 #include "internal.h"
 
@@ -36,9 +38,24 @@ __global__ void __launch_bounds__(1024)
     const int64_t base = sig * n + static_cast<int64_t>(t) * P;
 
     E v[P];
+    using V4 = typename Vec4Of<E>::type;
+    const bool vec4 = RAGGED && P % 4 == 0 && (n & 3) == 0;
     if constexpr (RAGGED) {
+        if (vec4) {
 #pragma unroll
-        for (int i = 0; i < P; ++i) v[i] = (active && t * P + i < n) ? in[base + i] : E(0);
+            for (int q = 0; q < (P >= 4 ? P / 4 : 0); ++q) {
+                const bool in_row = active && t * P + 4 * q < n;
+                V4 w = {};
+                if (in_row) w = ld_stream(reinterpret_cast<const V4 *>(in + base) + q);
+                v[4 * q] = w.x;
+                v[4 * q + 1] = w.y;
+                v[4 * q + 2] = w.z;
+                v[4 * q + 3] = w.w;
+            }
+        } else {
+#pragma unroll
+            for (int i = 0; i < P; ++i) v[i] = (active && t * P + i < n) ? in[base + i] : E(0);
+        }
     } else if (active) {
         load_run<E, P>(in + base, v);
     } else {
@@ -70,9 +87,22 @@ __global__ void __launch_bounds__(1024)
 #pragma unroll
     for (int i = 0; i < P; ++i) v[i] += excl;
     if constexpr (RAGGED) {
+        if (vec4) {
 #pragma unroll
-        for (int i = 0; i < P; ++i)
-            if (active && t * P + i < n) out[base + i] = v[i];
+            for (int q = 0; q < (P >= 4 ? P / 4 : 0); ++q)
+                if (active && t * P + 4 * q < n) {
+                    V4 w;
+                    w.x = v[4 * q];
+                    w.y = v[4 * q + 1];
+                    w.z = v[4 * q + 2];
+                    w.w = v[4 * q + 3];
+                    st_stream(reinterpret_cast<V4 *>(out + base) + q, w);
+                }
+        } else {
+#pragma unroll
+            for (int i = 0; i < P; ++i)
+                if (active && t * P + i < n) out[base + i] = v[i];
+        }
     } else if (active) {
         store_run<E, P>(out + base, v);
     }

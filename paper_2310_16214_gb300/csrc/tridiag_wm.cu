@@ -55,7 +55,8 @@ using wm::wm_warp_only;
 // RAGGED: systems of nrow < 2^logn equations (rows nrow apart), solved as
 // the power-of-two system padded with identity rows (a = c = 0, b = 1,
 // d = 0, whose unknowns are 0); c of the last real row is taken as 0 and
-// nothing past nrow is read or written.  Element-wise accesses there.
+// nothing past nrow is read or written.  Accesses are 16 bytes wide when
+// nrow is a multiple of 4 and P of 4, else element-wise.
 template <int P, int R, int SHUFFLE, int MAXT, bool RAGGED>
 __global__ void __launch_bounds__(MAXT)
     tridiag_wm_kernel(const float *ga, const float *gb, const float *gc, const float *gd, float *x, int logn,
@@ -75,16 +76,40 @@ __global__ void __launch_bounds__(MAXT)
         const int i0 = t * P;
         const int64_t g0 = (sig0 + s) * static_cast<int64_t>(nrow) + i0;
         float a[P], b[P], c[P], d[P];
+        // nrow a multiple of 4: rows start on 16-byte boundaries and a group of
+        // 4 equations is wholly inside or wholly past the system
+        const bool vec4 = P % 4 == 0 && (nrow & 3) == 0;
+        if (vec4) {
 #pragma unroll
-        for (int i = 0; i < P; ++i) {
-            const bool in = active && i0 + i < nrow;
-            a[i] = in ? ga[g0 + i] : 0.f;
-            b[i] = in ? gb[g0 + i] : 1.f;
-            c[i] = active && i0 + i < nrow - 1 ? gc[g0 + i] : 0.f;
-            d[i] = in ? gd[g0 + i] : 0.f;
+            for (int q = 0; q < (P >= 4 ? P / 4 : 0); ++q) {
+                const bool in = active && i0 + 4 * q < nrow;
+                float4 va = make_float4(0.f, 0.f, 0.f, 0.f), vb = make_float4(1.f, 1.f, 1.f, 1.f), vc = va, vd = va;
+                if (in) {
+                    va = __ldcs(reinterpret_cast<const float4 *>(ga + g0) + q);
+                    vb = __ldcs(reinterpret_cast<const float4 *>(gb + g0) + q);
+                    vc = __ldcs(reinterpret_cast<const float4 *>(gc + g0) + q);
+                    vd = __ldcs(reinterpret_cast<const float4 *>(gd + g0) + q);
+                }
+                a[4 * q] = va.x; a[4 * q + 1] = va.y; a[4 * q + 2] = va.z; a[4 * q + 3] = va.w;
+                b[4 * q] = vb.x; b[4 * q + 1] = vb.y; b[4 * q + 2] = vb.z; b[4 * q + 3] = vb.w;
+                c[4 * q] = vc.x; c[4 * q + 1] = vc.y; c[4 * q + 2] = vc.z; c[4 * q + 3] = vc.w;
+                d[4 * q] = vd.x; d[4 * q + 1] = vd.y; d[4 * q + 2] = vd.z; d[4 * q + 3] = vd.w;
+            }
+#pragma unroll
+            for (int i = 0; i < P; ++i)
+                if (i0 + i == nrow - 1) c[i] = 0.f;  // the last row's c is outside the matrix
+        } else {
+#pragma unroll
+            for (int i = 0; i < P; ++i) {
+                const bool in = active && i0 + i < nrow;
+                a[i] = in ? ga[g0 + i] : 0.f;
+                b[i] = in ? gb[g0 + i] : 1.f;
+                c[i] = active && i0 + i < nrow - 1 ? gc[g0 + i] : 0.f;
+                d[i] = in ? gd[g0 + i] : 0.f;
+            }
         }
         const int nval = nrow - i0 < 0 ? 0 : (nrow - i0 < P ? nrow - i0 : P);
-        wm::wm_solve_regs<P, R, SHUFFLE>(a, b, c, d, x + g0, active && nval > 0, log_tps, buf, nval, false);
+        wm::wm_solve_regs<P, R, SHUFFLE>(a, b, c, d, x + g0, active && nval > 0, log_tps, buf, nval, vec4);
     }
 }
 
