@@ -250,6 +250,19 @@ class Workload:
             p = self._plan(name, bp.OP_TRIDIAG, bp.F32, n, batch)
             self._add(name, "tridiag", n, batch, batch * n, 20 * batch * n,
                       (lambda ts=ts, x=x, n=n, b=batch, p=p: bp.tridiag_batched(*ts, x, n, b, plan=p)), ts, [x], p)
+        # Wang-Mou rows: only when named in --rows (the step's tridiagonal
+        # rows are the CR/PCR hybrid the configuration names)
+        for n in TRI_SIZES:
+            name = "tridiag_wm_%d" % n
+            if self.rows is None or name not in self.rows:
+                continue
+            batch = max(1, int(TRI_TOTAL * scale) // n)
+            a, b, c, d, _ = si.tridiag_f32(batch, n, stream=200 + n)
+            ts = [t.from_numpy(v).to(dev) for v in (a, b, c, d)]
+            x = t.empty_like(ts[0])
+            p = self._plan(name, bp.OP_TRIDIAG_WM, bp.F32, n, batch)
+            self._add(name, "tridiag_wm", n, batch, batch * n, 20 * batch * n,
+                      (lambda ts=ts, x=x, n=n, b=batch, p=p: bp.tridiag_batched(*ts, x, n, b, plan=p)), ts, [x], p)
         name = "refined_%d" % REF_N
         if self._want(name):
             batch = max(1, int(REF_BATCH * scale))
@@ -449,7 +462,8 @@ def run_ours(args):
                               "gb_s": round(it["bytes"] / (per_item[it["name"]] * 1e-3) / 1e9, 1),
                               "plan": {k: v for k, v in it["plan"].as_dict().items()
                                        if k in ("P", "L", "spb", "smem_layout", "smem_pad", "io", "cr_switch",
-                                                "shuffle", "pattern")}}
+                                                "shuffle", "pattern")
+                                       or (k == "radix" and it["op"] == "tridiag_wm")}}
                  for it in wl.items}
 
     ext = None
