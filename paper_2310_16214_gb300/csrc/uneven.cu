@@ -14,8 +14,9 @@
 //   FFT      512 threads, two blocks per SM; radix 16 (mixed-radix first
 //            stage), T = n / 16, every size with the compile-time stage
 //            schedule (one non-inlined function per size)
-//   tridiag  1024 threads; P = 8; the Wang-Mou divide and conquer (each
-//            thread's 8 equations by a Thomas sweep, then radix-2 merges)
+//   tridiag  512 threads, two blocks per SM; P = 16; the Wang-Mou divide and
+//            conquer (each thread's 16 equations by a Thomas sweep, then
+//            radix-2 merges)
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -44,7 +45,7 @@ struct UnitDesc {
 
 constexpr int kUnevenScanThreads = 256;
 constexpr int kUnevenFftThreads = 512;
-constexpr int kUnevenTriThreads = 1024;
+constexpr int kUnevenTriThreads = 512;
 constexpr int kUnevenMinLog = 5;
 constexpr int kUnevenMaxLog = 13;
 
@@ -193,7 +194,7 @@ __global__ void __launch_bounds__(kUnevenFftThreads, 2)
 // (Feeding the next unit through a shared-memory slot while one is solved
 // was measured slower, with per-thread asynchronous copies and with bulk
 // copies alike: 76 and 90 us against 53 us for the 4096-system batch.)
-constexpr int kUnevenTriP = 8;
+constexpr int kUnevenTriP = 16;
 
 template <int P>
 __device__ __forceinline__ void tri_unit(const ItemDesc *items, const UnitDesc &U, float4 *smem) {
@@ -215,7 +216,7 @@ __device__ __forceinline__ void tri_unit(const ItemDesc *items, const UnitDesc &
     wm::wm_solve<P, 2, 1>(ga, gb, gc, gd, x, active, log_tps, smem);
 }
 
-__global__ void __launch_bounds__(kUnevenTriThreads)
+__global__ void __launch_bounds__(kUnevenTriThreads, 2)
     uneven_tri_kernel(const ItemDesc *items, const UnitDesc *units, int nunits, int *counter) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ int s_unit;
