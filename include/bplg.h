@@ -289,8 +289,8 @@ typedef struct bplg_uneven_batch *bplg_uneven_handle;
 /* Prepare an uneven batch on the current device: validate the items, group
  * them by (operation, size) into units (largest first), copy the descriptors
  * to library-owned device memory, and capture into a CUDA graph one counter
- * reset plus three persistent kernels (scan, FFT, tridiag) that pull units
- * from an atomic counter each.  The item buffers must stay valid while the
+ * reset plus three persistent kernels (scan, radix-16 Stockham FFT, and the
+ * Wang-Mou tridiagonal solver) that pull units from an atomic counter each.  The item buffers must stay valid while the
  * handle is used.  Synchronous; allocates.
  * Errors: INVALID_ARG, UNSUPPORTED_SIZE, CUDA. */
 int bplg_uneven_create(const bplg_item *items, int64_t count, bplg_uneven_handle *out);
