@@ -99,7 +99,9 @@ typedef enum { BPLG_TC_BF16 = 0, BPLG_TC_F16 = 1 } bplg_tc_precision;
  *           equation in registers (register-level CR), 5 the same with the
  *           coefficients held as float64 registers and their float32
  *           copies in shared memory (P <= 8), 6 the same with the float32
- *           coefficients in shared memory only (fewer registers per thread).
+ *           coefficients in shared memory only (fewer registers per thread),
+ *           7 as 6 with the float32 solves done by the Wang-Mou divide and
+ *           conquer (radix 2; shuffle 1, smem_pad 0, cr_switch 32).
  *   smem_pad 1: pad shared-memory rows against bank conflicts.
  *   io      FFT: 0 registers <-> global memory directly, 1 staged through
  *           shared memory with 16-byte accesses, 2 persistent blocks fed by

@@ -131,9 +131,10 @@ bool plan_structurally_valid(const bplg_plan &p, int dtype, int64_t n, std::stri
                 return fail(why, "tridiag: shuffle/pad out of range");
             if (p.shuffle && p.cr_switch > 32) return fail(why, "tridiag: shuffle PCR needs cr_switch <= 32");
             if (p.op == BPLG_OP_TRIDIAG_REFINED && tps < 32) return fail(why, "refined: at least 32 threads per system");
-            if (p.smem_layout < 0 || p.smem_layout > (p.op == BPLG_OP_TRIDIAG_REFINED ? 6 : 2))
+            if (p.smem_layout < 0 || p.smem_layout > (p.op == BPLG_OP_TRIDIAG_REFINED ? 7 : 2))
                 return fail(why, "tridiag: smem_layout out of range (0 strided rows, 1 compacted levels, 2 register "
-                                 "levels; refined: bit 0 float64 coefficients, bit 1 compacted levels, 4-6 register levels)");
+                                 "levels; refined: bit 0 float64 coefficients, bit 1 compacted levels, 4-6 register levels, "
+                                 "7 Wang-Mou solves)");
             if (p.op == BPLG_OP_TRIDIAG && p.smem_layout == 2 && (p.P < 2 || (p.io == 1 && (p.P < 4 || n < 64))))
                 return fail(why, "tridiag: register levels need P >= 2 (P >= 4 and n >= 64 when pipelined)");
             if (p.op == BPLG_OP_TRIDIAG && p.smem_layout == 1 && (p.smem_pad != 1 || p.io != 0))
@@ -142,6 +143,9 @@ bool plan_structurally_valid(const bplg_plan &p, int dtype, int64_t n, std::stri
                 return fail(why, "refined: the compacted layout is always padded");
             if (p.op == BPLG_OP_TRIDIAG_REFINED && p.smem_layout >= 4 && (p.P < 2 || (p.smem_layout == 5 && p.P > 8)))
                 return fail(why, "refined: register levels need P >= 2 (P <= 8 with float64 coefficients)");
+            if (p.op == BPLG_OP_TRIDIAG_REFINED && p.smem_layout == 7 &&
+                (p.shuffle != 1 || p.smem_pad != 0 || p.cr_switch != 32))
+                return fail(why, "refined: the Wang-Mou layout takes shuffle 1, pad 0 and cr_switch 32 (unused)");
             if (p.io < 0 || p.io > (p.op == BPLG_OP_TRIDIAG ? 1 : 0))
                 return fail(why, "tridiag: io out of range (0 per-block, 1 pipelined)");
             if (p.io == 1 && n < 4) return fail(why, "tridiag: the pipelined kernel needs n >= 4");
@@ -271,7 +275,7 @@ std::vector<bplg_plan> enumerate_structural(int op, int dtype, int64_t n) {
                 }
             } else {
                 const int64_t mmax = tps < n ? tps : n;
-                const int layouts = op == BPLG_OP_TRIDIAG_REFINED ? 7 : 3;
+                const int layouts = op == BPLG_OP_TRIDIAG_REFINED ? 8 : 3;
                 const int ios = op == BPLG_OP_TRIDIAG ? 2 : 1;
                 for (int io = ios - 1; io >= 0; --io) {
                     for (int lay = layouts - 1; lay >= 0; --lay) {

@@ -42,6 +42,7 @@
 #include "internal.h"
 #include "tma.cuh"
 #include "tridiag_common.cuh"
+#include "tridiag_wm.cuh"
 
 namespace bplg {
 
@@ -820,8 +821,10 @@ __global__ void __launch_bounds__(1024)
 // layout 6) as float32 rows in shared memory only, which frees 4P registers
 // per thread for occupancy.  Shared-memory rows are stored [row][thread] so a
 // warp's float4 accesses are contiguous.  The arithmetic is that of the
-// shared-memory refinement.
-template <int P, int CO, int PAD, int SHUFFLE, int MAXT>
+// shared-memory refinement.  With SOLVER = 1 (refined smem_layout 7, the
+// coefficients as in layout 6) the float32 solves are the Wang-Mou divide
+// and conquer (radix-2 merges, shuffles within a warp) instead of CR/PCR.
+template <int P, int CO, int PAD, int SHUFFLE, int MAXT, int SOLVER = 0>
 __global__ void __launch_bounds__(MAXT)
     tridiag_refined_reg_kernel(const float *ga, const float *gb, const float *gc, const float *gd, double *x,
                                int32_t *iters, int logn, int log_m, int log_tps, int spb, int64_t batch,
@@ -845,8 +848,10 @@ __global__ void __launch_bounds__(MAXT)
     const int mstride = tstride<PAD>(tps);
     float4 *rows = reinterpret_cast<float4 *>(smem_raw) + s * mstride;
     float4 *bnd = reinterpret_cast<float4 *>(smem_raw) + spb * mstride;
-    double *xfirst = reinterpret_cast<double *>(reinterpret_cast<float4 *>(smem_raw) + spb * mstride +
-                                                blockDim.x * LP);
+    // Wang-Mou exchange buffer (4 float4 per thread) in place of rows + bnd
+    float4 *wbuf = reinterpret_cast<float4 *>(smem_raw);
+    double *xfirst = reinterpret_cast<double *>(reinterpret_cast<float4 *>(smem_raw) +
+                                                (SOLVER ? 4 * blockDim.x : spb * mstride + blockDim.x * LP));
     double *xlast = xfirst + blockDim.x;
     // layouts 5 and 6: row i of this thread at ocoef[i * blockDim.x]
     float4 *ocoef = reinterpret_cast<float4 *>(xlast + blockDim.x) + tid;
@@ -901,7 +906,11 @@ __global__ void __launch_bounds__(MAXT)
     // la..ld become the working copy
     if (t == 0) done_sys[s] = valid ? 0 : 1;
     const bool single = spb == 1;  // (then the block's one system is valid)
-    cr_register_solve<P, PAD, SHUFFLE>(la, lb, lc, ld, log_m, log_tps, t, rows, bnd);
+    if constexpr (SOLVER == 1) {
+        wm::wm_solve_inreg<P, 2, 1>(la, lb, lc, ld, log_tps, wbuf);
+    } else {
+        cr_register_solve<P, PAD, SHUFFLE>(la, lb, lc, ld, log_m, log_tps, t, rows, bnd);
+    }
     double xs[P];
     float xmaxf = 0.f;
 #pragma unroll
@@ -991,7 +1000,11 @@ __global__ void __launch_bounds__(MAXT)
         const float sigma = pow2_f32(-ex);
 #pragma unroll
         for (int i = 0; i < P; ++i) ld[i] *= sigma;
-        cr_register_solve<P, PAD, SHUFFLE>(la, lb, lc, ld, log_m, log_tps, t, rows, bnd);
+        if constexpr (SOLVER == 1) {
+            wm::wm_solve_inreg<P, 2, 1>(la, lb, lc, ld, log_tps, wbuf);
+        } else {
+            cr_register_solve<P, PAD, SHUFFLE>(la, lb, lc, ld, log_m, log_tps, t, rows, bnd);
+        }
         const bool was_done = (!single && done_sys[s] != 0) || rmaxf == 0.f;
         float emaxf = 0.f;
 #pragma unroll
@@ -1025,6 +1038,18 @@ namespace {
 // refined: layout bit 0 = float64 coefficient cache, bit 1 = compacted solver
 template <int PAD, int SHUFFLE>
 const void *tri_func_ps(bool refined, int layout, int io, int P) {
+    if (refined && layout == 7) {  // Wang-Mou solves: unpadded, shuffle merges only
+        if constexpr (PAD == 0 && SHUFFLE == 1) {
+            switch (P) {
+                case 2: return reinterpret_cast<const void *>(&tridiag_refined_reg_kernel<2, 2, 0, 1, 1024, 1>);
+                case 4: return reinterpret_cast<const void *>(&tridiag_refined_reg_kernel<4, 2, 0, 1, 1024, 1>);
+                case 8: return reinterpret_cast<const void *>(&tridiag_refined_reg_kernel<8, 2, 0, 1, 512, 1>);
+                case 16: return reinterpret_cast<const void *>(&tridiag_refined_reg_kernel<16, 2, 0, 1, 256, 1>);
+                default: return nullptr;
+            }
+        }
+        return nullptr;
+    }
     if (refined && layout >= 4) {
         switch (layout * 32 + P) {
             case 4 * 32 + 2: return reinterpret_cast<const void *>(&tridiag_refined_reg_kernel<2, 0, PAD, SHUFFLE, 1024>);
@@ -1072,7 +1097,7 @@ const void *tri_func_ps(bool refined, int layout, int io, int P) {
 }
 
 const void *tri_func(int pad, int shuffle, bool refined, int layout, int io, int P) {
-    if (pad < 0 || pad > 1 || shuffle < 0 || shuffle > 1 || layout < 0 || layout > 6 || io < 0 || io > 1)
+    if (pad < 0 || pad > 1 || shuffle < 0 || shuffle > 1 || layout < 0 || layout > 7 || io < 0 || io > 1)
         return nullptr;
     if (!refined && layout == 1 && (pad != 1 || io != 0)) return nullptr;
     if (!refined && layout == 2 && io == 1 && P < 4) return nullptr;
@@ -1095,6 +1120,10 @@ int tridiag_smem_bytes(int pad, int64_t n, int spb, bool refined, int layout, in
     }
     if (!refined && io == 1) return kTriTmaStages * 16 * spb * ni + spb * 16 * (pad ? tstride<1>(ni) : ni);
     if (!refined) return spb * 16 * (pad ? tstride<1>(ni) : ni);
+    if (layout == 7) {  // Wang-Mou exchanges + neighbour x slots + coefficient rows
+        const int threads = spb * (ni / P);
+        return threads * 64 + threads * 16 + spb * ni * 16;
+    }
     if (layout >= 4) {  // register refinement: middle rows + boundary slots + neighbour x slots (+ rows)
         const int tps = ni / P;
         const int lp = ilog2(P);

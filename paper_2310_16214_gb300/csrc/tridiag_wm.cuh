@@ -113,17 +113,13 @@ __host__ __device__ __forceinline__ bool wm_warp_only(int shuffle, int64_t tps) 
 
 // One system (or, with several systems per block, each of them) solved by
 // the threads that serve it, from this thread's P equations in registers
-// (identity rows where `active` is false; a..d are destroyed).  x points at
-// the thread's P unknowns, of which the first `nval` are written (fewer
-// than P only in the last run of a padded system); with `vec` false every
-// store is element-wise (rows of a padded system need not be 16-byte
-// aligned).  buf is the block's
-// shared memory (4 float4 per thread) unless every exchange is a warp
-// shuffle.  Every thread of the block calls it.
+// (identity rows where `active` is false).  a..c are destroyed and d ends
+// holding the thread's P unknowns.  buf is the block's shared memory (4
+// float4 per thread) unless every exchange is a warp shuffle.  Every thread
+// of the block calls it.
 template <int P, int R, int SHUFFLE>
-__device__ __forceinline__ void wm_solve_regs(float (&a)[P], float (&b)[P], float (&c)[P], float (&d)[P], float *x,
-                                              bool active, int log_tps, float4 *buf, int nval = P,
-                                              bool vec = true) {
+__device__ __forceinline__ void wm_solve_inreg(float (&a)[P], float (&b)[P], float (&c)[P], float (&d)[P],
+                                               int log_tps, float4 *buf) {
     const int tps = 1 << log_tps;
     const int tid = threadIdx.x;
     const int t = tid & (tps - 1);
@@ -192,16 +188,26 @@ __device__ __forceinline__ void wm_solve_regs(float (&a)[P], float (&b)[P], floa
         xl_nb = t > 0 ? xb[tid - 1].y : 0.f;
         xr_nb = t < tps - 1 ? xb[tid + 1].x : 0.f;
     }
-    float xv[P];
 #pragma unroll
-    for (int i = 0; i < P; ++i) xv[i] = fmaf(gm[i], xr_nb, fmaf(be[i], xl_nb, al[i]));
+    for (int i = 0; i < P; ++i) d[i] = fmaf(gm[i], xr_nb, fmaf(be[i], xl_nb, al[i]));
+}
+
+// The same, then the unknowns stored: x points at the thread's P unknowns,
+// of which the first `nval` are written (fewer than P only in the last run
+// of a padded system); with `vec` false every store is element-wise (rows of
+// a padded system need not be 16-byte aligned).
+template <int P, int R, int SHUFFLE>
+__device__ __forceinline__ void wm_solve_regs(float (&a)[P], float (&b)[P], float (&c)[P], float (&d)[P], float *x,
+                                              bool active, int log_tps, float4 *buf, int nval = P,
+                                              bool vec = true) {
+    wm_solve_inreg<P, R, SHUFFLE>(a, b, c, d, log_tps, buf);
     if (active) {
         if (vec && nval >= P) {
-            store_run<float, P>(x, xv);
+            store_run<float, P>(x, d);
         } else {
 #pragma unroll
             for (int i = 0; i < P; ++i)
-                if (i < nval) x[i] = xv[i];
+                if (i < nval) x[i] = d[i];
         }
     }
 }

@@ -250,7 +250,7 @@ struct SplitMix {
 std::vector<double> raw_features(const bplg_plan &p) {
     std::vector<double> f = {std::log2(double(p.P)), std::log2(double(p.spb)), double(p.pattern),
                              double(p.smem_pad), std::log2(double(std::max(1, p.cr_switch))), double(p.shuffle)};
-    for (int k = 0; k < 7; ++k) f.push_back(p.smem_layout == k ? 1.0 : 0.0);
+    for (int k = 0; k < 8; ++k) f.push_back(p.smem_layout == k ? 1.0 : 0.0);
     for (int k = 0; k < 3; ++k) f.push_back(p.io == k ? 1.0 : 0.0);
     // the merge radix of the Wang-Mou solver (a constant column elsewhere,
     // dropped by the normalisation)
