@@ -608,8 +608,9 @@ def measure_e2e(torch, wl, stream, args):
     are copied from pinned host memory, the row runs, and its outputs are
     copied back, all inside the timed region.  Copies in, compute and copies
     out go to three streams (the library calls take the stream): row k's
-    outputs move out while row k+1's inputs move in (the link is full duplex);
-    rows that share buffers are ordered by stream waits."""
+    outputs move out while row k+1's inputs move in (the link is full duplex),
+    and row k+1's inputs may move in while row k runs; rows that share
+    buffers are ordered by stream waits."""
     host_in, host_out = {}, {}
     h2d = d2h = 0
     for it in wl.items:
@@ -621,20 +622,34 @@ def measure_e2e(torch, wl, stream, args):
     s_out = torch.cuda.Stream()
     s_comp = torch.cuda.Stream()
 
+    # rows that share a device buffer with an earlier row (the inverse FFT row
+    # after the forward one of the same size) wait for it; every other row's
+    # inputs move in while earlier rows run
+    def ptrs(it):
+        return {x.data_ptr() for x in it["ins"] + it["outs"]}
+
+    items = wl.items
+    shares_earlier = [any(ptrs(items[j]) & ptrs(items[k]) for j in range(k)) for k in range(len(items))]
+
     def step():
-        for it in wl.items:
+        for k, it in enumerate(items):
+            if shares_earlier[k]:
+                s_in.wait_stream(s_comp)  # earlier rows have finished with the shared buffers
             with torch.cuda.stream(s_in):
                 for hx, dx in zip(host_in[it["name"]], it["ins"]):
                     dx.copy_(hx, non_blocking=True)
             s_comp.wait_stream(s_in)
-            s_comp.wait_stream(s_out)  # rows may share output buffers with the previous row
+            if k == 0 or shares_earlier[k]:
+                # earlier output copies have left the shared buffers (at the
+                # start of a step: every output copy of the previous step)
+                s_comp.wait_stream(s_out)
             with torch.cuda.stream(s_comp):
                 it["fn"]()  # the binding launches on the current stream
             s_out.wait_stream(s_comp)
             with torch.cuda.stream(s_out):
                 for hx, dx in zip(host_out[it["name"]], it["outs"]):
                     hx.copy_(dx, non_blocking=True)
-            s_in.wait_stream(s_comp)  # the next row may overwrite shared inputs only after this row ran
+        s_in.wait_stream(s_comp)  # the next step's inputs overwrite this step's
 
     steps = max(1, min(args.steps, 5))
     step()
