@@ -824,11 +824,10 @@ __global__ void __launch_bounds__(1024)
 // shared-memory refinement.  With SOLVER = 1 (refined smem_layout 7, the
 // coefficients as in layout 6) the float32 solves are the Wang-Mou divide
 // and conquer (radix-2 merges, shuffles within a warp) instead of CR/PCR.
-template <int P, int CO, int PAD, int SHUFFLE, int MAXT, int SOLVER = 0>
-__global__ void __launch_bounds__(MAXT)
-    tridiag_refined_reg_kernel(const float *ga, const float *gb, const float *gc, const float *gd, double *x,
-                               int32_t *iters, int logn, int log_m, int log_tps, int spb, int64_t batch,
-                               int max_iter, float tolf) {
+template <int P, int CO, int PAD, int SHUFFLE, int SOLVER>
+__device__ __forceinline__ void refined_reg_body(const float *ga, const float *gb, const float *gc, const float *gd,
+                                                 double *x, int32_t *iters, int logn, int log_m, int log_tps, int spb,
+                                                 int64_t batch, int max_iter, float tolf) {
     constexpr int LP = (P >= 16) ? 4 : (P >= 8) ? 3 : (P >= 4) ? 2 : 1;
     constexpr int PF = CO == 0 ? P : 1;  // float32 coefficient registers (layout 4)
     constexpr int PD = CO == 1 ? P : 1;  // float64 coefficient registers (layout 5)
@@ -1033,17 +1032,44 @@ __global__ void __launch_bounds__(MAXT)
     }
 }
 
+template <int P, int CO, int PAD, int SHUFFLE, int MAXT, int SOLVER = 0>
+__global__ void __launch_bounds__(MAXT)
+    tridiag_refined_reg_kernel(const float *ga, const float *gb, const float *gc, const float *gd, double *x,
+                               int32_t *iters, int logn, int log_m, int log_tps, int spb, int64_t batch,
+                               int max_iter, float tolf) {
+    refined_reg_body<P, CO, PAD, SHUFFLE, SOLVER>(ga, gb, gc, gd, x, iters, logn, log_m, log_tps, spb, batch,
+                                                  max_iter, tolf);
+}
+
+// The same for blocks of at most MAXT threads with MINB of them resident per
+// SM: the register cap that follows (65536 / (MAXT MINB)) trades a few
+// spilled bytes for more resident warps.  Used by the Wang-Mou layout with
+// P = 8 and blocks of up to 128 threads: 80 registers, 6 blocks per SM
+// (0.266 against 0.287 ms at n = 1024; the P = 16 form capped at 96
+// registers spilled 432 bytes and ran slower).
+template <int P, int CO, int PAD, int SHUFFLE, int MAXT, int SOLVER, int MINB>
+__global__ void __launch_bounds__(MAXT, MINB)
+    tridiag_refined_reg_kernel_mb(const float *ga, const float *gb, const float *gc, const float *gd, double *x,
+                                  int32_t *iters, int logn, int log_m, int log_tps, int spb, int64_t batch,
+                                  int max_iter, float tolf) {
+    refined_reg_body<P, CO, PAD, SHUFFLE, SOLVER>(ga, gb, gc, gd, x, iters, logn, log_m, log_tps, spb, batch,
+                                                  max_iter, tolf);
+}
+
 namespace {
 
 // refined: layout bit 0 = float64 coefficient cache, bit 1 = compacted solver
 template <int PAD, int SHUFFLE>
-const void *tri_func_ps(bool refined, int layout, int io, int P) {
+const void *tri_func_ps(bool refined, int layout, int io, int P, int threads) {
     if (refined && layout == 7) {  // Wang-Mou solves: unpadded, shuffle merges only
         if constexpr (PAD == 0 && SHUFFLE == 1) {
             switch (P) {
                 case 2: return reinterpret_cast<const void *>(&tridiag_refined_reg_kernel<2, 2, 0, 1, 1024, 1>);
                 case 4: return reinterpret_cast<const void *>(&tridiag_refined_reg_kernel<4, 2, 0, 1, 1024, 1>);
-                case 8: return reinterpret_cast<const void *>(&tridiag_refined_reg_kernel<8, 2, 0, 1, 512, 1>);
+                case 8:
+                    if (threads <= 128)  // 80 registers: 6 blocks per SM
+                        return reinterpret_cast<const void *>(&tridiag_refined_reg_kernel_mb<8, 2, 0, 1, 128, 1, 6>);
+                    return reinterpret_cast<const void *>(&tridiag_refined_reg_kernel<8, 2, 0, 1, 512, 1>);
                 case 16: return reinterpret_cast<const void *>(&tridiag_refined_reg_kernel<16, 2, 0, 1, 256, 1>);
                 default: return nullptr;
             }
@@ -1096,13 +1122,15 @@ const void *tri_func_ps(bool refined, int layout, int io, int P) {
     return reinterpret_cast<const void *>(&tridiag_kernel<PAD, SHUFFLE>);
 }
 
-const void *tri_func(int pad, int shuffle, bool refined, int layout, int io, int P) {
+const void *tri_func(int pad, int shuffle, bool refined, int layout, int io, int P, int threads) {
     if (pad < 0 || pad > 1 || shuffle < 0 || shuffle > 1 || layout < 0 || layout > 7 || io < 0 || io > 1)
         return nullptr;
     if (!refined && layout == 1 && (pad != 1 || io != 0)) return nullptr;
     if (!refined && layout == 2 && io == 1 && P < 4) return nullptr;
-    if (pad) return shuffle ? tri_func_ps<1, 1>(refined, layout, io, P) : tri_func_ps<1, 0>(refined, layout, io, P);
-    return shuffle ? tri_func_ps<0, 1>(refined, layout, io, P) : tri_func_ps<0, 0>(refined, layout, io, P);
+    if (pad)
+        return shuffle ? tri_func_ps<1, 1>(refined, layout, io, P, threads)
+                       : tri_func_ps<1, 0>(refined, layout, io, P, threads);
+    return shuffle ? tri_func_ps<0, 1>(refined, layout, io, P, threads) : tri_func_ps<0, 0>(refined, layout, io, P, threads);
 }
 
 }  // namespace
@@ -1145,7 +1173,7 @@ bool tridiag_launch_info(const bplg_plan &p, int64_t n, int64_t batch, bool refi
     std::string why;
     bplg_plan q = p;
     if (!plan_structurally_valid(q, BPLG_F32, n, &why)) return false;
-    const void *f = tri_func(p.smem_pad, p.shuffle, refined, p.smem_layout, refined ? 0 : p.io, p.P);
+    const void *f = tri_func(p.smem_pad, p.shuffle, refined, p.smem_layout, refined ? 0 : p.io, p.P, p.L);
     if (!f) return false;
     out->func = f;
     out->threads = p.L;
