@@ -1,6 +1,7 @@
 // Device code of the Wang-Mou divide-and-conquer tridiagonal solver, shared
-// by the batched kernel (tridiag_wm.cu) and the uneven-batch kernel.  The
-// method and its mapping are described in tridiag_wm.cu.
+// by the batched kernel (tridiag_wm.cu), the uneven-batch kernel and the
+// float32 solves of the refined kernel (layout 7).  The method and its
+// mapping are described in tridiag_wm.cu.
 #pragma once
 
 #include <cuda_runtime.h>
