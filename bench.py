@@ -80,9 +80,9 @@ NCU_TRAFFIC = {
     # half-size launch, doubled (the rest of x is still in L2 at kernel end)
     ("refined_1024", (("P", 16), ("L", 64), ("spb", 1), ("shuffle", 1), ("pattern", 0), ("smem_layout", 6),
                       ("smem_pad", 0), ("io", 0), ("cr_switch", 32))): 2 * (134331648 + 26756608),
-    # the Wang-Mou layout (7), P = 8: tridiag_refined_reg_kernel_mb (80 registers)
+    # the Wang-Mou layout (7), P = 8: tridiag_refined_reg_kernel_mb (72 registers)
     ("refined_1024", (("P", 8), ("L", 128), ("spb", 1), ("shuffle", 1), ("pattern", 0), ("smem_layout", 7),
-                      ("smem_pad", 0), ("io", 0), ("cr_switch", 32))): 2 * (134295040 + 29300480),
+                      ("smem_pad", 0), ("io", 0), ("cr_switch", 32))): 2 * (134292992 + 27802368),
 }
 
 # FP64 issue rate of one SM: 2 double-precision fused multiply-adds per clock

@@ -1044,9 +1044,10 @@ __global__ void __launch_bounds__(MAXT)
 // The same for blocks of at most MAXT threads with MINB of them resident per
 // SM: the register cap that follows (65536 / (MAXT MINB)) trades a few
 // spilled bytes for more resident warps.  Used by the Wang-Mou layout with
-// P = 8 and blocks of up to 128 threads: 80 registers, 6 blocks per SM
-// (0.266 against 0.287 ms at n = 1024; the P = 16 form capped at 96
-// registers spilled 432 bytes and ran slower).
+// P = 8 and blocks of up to 128 threads: 72 registers, 7 blocks per SM
+// (0.256 ms at n = 1024, against 0.287 ms uncapped, 0.266 ms at 80 registers
+// and 0.272 ms at 64; the P = 16 form capped at 96 registers spilled 432
+// bytes and ran slower).
 template <int P, int CO, int PAD, int SHUFFLE, int MAXT, int SOLVER, int MINB>
 __global__ void __launch_bounds__(MAXT, MINB)
     tridiag_refined_reg_kernel_mb(const float *ga, const float *gb, const float *gc, const float *gd, double *x,
@@ -1067,8 +1068,8 @@ const void *tri_func_ps(bool refined, int layout, int io, int P, int threads) {
                 case 2: return reinterpret_cast<const void *>(&tridiag_refined_reg_kernel<2, 2, 0, 1, 1024, 1>);
                 case 4: return reinterpret_cast<const void *>(&tridiag_refined_reg_kernel<4, 2, 0, 1, 1024, 1>);
                 case 8:
-                    if (threads <= 128)  // 80 registers: 6 blocks per SM
-                        return reinterpret_cast<const void *>(&tridiag_refined_reg_kernel_mb<8, 2, 0, 1, 128, 1, 6>);
+                    if (threads <= 128)  // 72 registers: 7 blocks per SM
+                        return reinterpret_cast<const void *>(&tridiag_refined_reg_kernel_mb<8, 2, 0, 1, 128, 1, 7>);
                     return reinterpret_cast<const void *>(&tridiag_refined_reg_kernel<8, 2, 0, 1, 512, 1>);
                 case 16: return reinterpret_cast<const void *>(&tridiag_refined_reg_kernel<16, 2, 0, 1, 256, 1>);
                 default: return nullptr;
