@@ -74,6 +74,21 @@ def test_in_place_and_closed_forms(bp):
     assert bp.device_status() == 0
 
 
+def test_maximum_size(bp):
+    # n = 2^24, the largest supported length: one random signal against the
+    # oracle, and a tone whose transform is n at one bin
+    n = 1 << 24
+    z = si.fft_c64(1, n, stream=24)
+    assert fft_rel_err(run(bp, z, -1), oracle.fft(z, -1)).max() <= 1e-5 * 24
+    k0 = 123457
+    k = np.arange(n, dtype=np.int64)
+    tone = np.exp(2j * np.pi * ((k0 * k) % n) / n).astype(np.complex64)[None, :]
+    X = run(bp, tone, -1)[0]
+    assert abs(X[k0] - n) < 1e-4 * n
+    assert np.max(np.abs(np.delete(X, k0))) < 1e-4 * n
+    assert bp.device_status() == 0
+
+
 def test_sizes_beyond_the_limit_are_rejected(bp):
     v = torch.zeros(16, dtype=torch.float32, device="cuda")
     # through the C ABI with raw pointers: rejected on the size, before any launch

@@ -140,7 +140,7 @@ def test_fft_bluestein_round_trip_and_in_place(bp):
     assert fft_rel_err(y, x.astype(np.complex128)).max() <= 2 * tol(n)
 
 
-@pytest.mark.parametrize("n", [100003, 1 << 20 | 1])
+@pytest.mark.parametrize("n", [100003, 1 << 20 | 1, (1 << 23) - 1])
 def test_fft_bluestein_large_closed_forms(bp, n):
     # an impulse at j0 gives exp(-2 pi i j0 k / n); a tone at f gives n at f
     k = np.arange(n, dtype=np.float64)
