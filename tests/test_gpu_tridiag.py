@@ -108,6 +108,20 @@ def test_refined_full_config_sampled(bp):
     assert it.min() >= 1
 
 
+@pytest.mark.parametrize("P", [8, 16])
+def test_refined_wang_mou_full_config_sampled(bp, P):
+    # the benchmark's tuned layout (Wang-Mou solves; P = 8 runs the
+    # register-capped form) at the full precision configuration
+    n, batch = 1024, 1 << 14
+    sysm = si.tridiag_f32(batch, n, seed=si.CONFIG_SEEDS["precision"])
+    p = bp.make_plan(bp.OP_TRIDIAG_REFINED, n, P, 1, shuffle=1, smem_layout=7, smem_pad=0, cr_switch=32)
+    x, it = run_refined(bp, sysm, plan=p, tol=1e-12)
+    rows = sample_rows(batch)
+    ref = oracle.thomas(*[v[rows] for v in sysm[:4]])
+    assert tri_rel_err(x[rows], ref).max() <= 1e-12
+    assert it.min() >= 1 and it.max() <= 10
+
+
 def test_refined_at_the_target_tolerance(bp):
     # stopping at tol = 1e-12 (the benchmark's setting) still meets 1e-12
     n, batch = 1024, 256
