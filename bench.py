@@ -99,13 +99,38 @@ def plan_key(plan):
                                      "cr_switch"))
 
 
-def dominant_roofline(dom, dom_ms, peak, peak_kind, refined_iters, clocks):
+def measure_fp64_peak(torch):
+    """The FP64 pipe's throughput measured on this GPU: eight independent
+    chains of double-precision fused multiply-adds per thread on every SM at
+    full residency (extref_fp64_fma, a measurement kernel outside the
+    library), best of 5 event-timed launches of about 16 ms each.  Returns
+    (TFLOP/s, description) or (None, reason)."""
+    import ctypes
+    try:
+        lib = ctypes.CDLL(os.path.join(ROOT, "paper_2310_16214_gb300", "_lib", "libbplg_extref.so"))
+        lib.extref_fp64_fma.argtypes = [ctypes.c_int64, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
+                                        ctypes.POINTER(ctypes.c_double), ctypes.c_void_p]
+        tf, ms = ctypes.c_double(), ctypes.c_double()
+        iters = 4096
+        rc = lib.extref_fp64_fma(iters, 5, ctypes.byref(tf), ctypes.byref(ms),
+                                 ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+        if rc != 0:
+            return None, "extref_fp64_fma returned %d" % rc
+        return tf.value, ("measured: DFMA chains (8 per thread, %d iterations, SMs x 8 blocks of 256 threads), "
+                          "best of 5 launches of %.1f ms" % (iters, ms.value))
+    except Exception as exc:
+        return None, "unavailable: %s" % str(exc)[:120]
+
+
+def dominant_roofline(dom, dom_ms, peak, peak_kind, refined_iters, clocks, fp64_peak=None):
     """Roofline of the step's longest launch.
 
     The refined solve is bound by the FP64 pipe, not by HBM: its algorithmic
     work is 3 FP64 fused multiply-adds (6 flop) per unknown for every residual
     and one FP64 add per unknown for every correction, with one residual more
-    than corrections (the last residual proves convergence).  Every other row
+    than corrections (the last residual proves convergence).  Its peak is the
+    FP64 rate measured by measure_fp64_peak (else derived from the SM count,
+    2 FP64 FMA per SM per clock and the maximum SM clock).  Every other row
     moves its algorithmic bytes once and is reported against HBM bandwidth."""
     traffic = NCU_TRAFFIC.get((dom["name"], plan_key(dom["plan"])))
     gbs = dom["bytes"] / (dom_ms * 1e-3) / 1e9
@@ -115,12 +140,17 @@ def dominant_roofline(dom, dom_ms, peak, peak_kind, refined_iters, clocks):
         flops = dom["elems"] * (6.0 * (c + 1.0) + c)
         sms = torch.cuda.get_device_properties(0).multi_processor_count
         mhz = clocks.get("sm_max_mhz") or DEFAULT_SM_MHZ
-        fp64_peak = sms * FP64_FMA_PER_SM_CLK * 2 * mhz * 1e6 / 1e12
+        derived = sms * FP64_FMA_PER_SM_CLK * 2 * mhz * 1e6 / 1e12
+        if fp64_peak and fp64_peak[0]:
+            fp64, kind = fp64_peak[0], fp64_peak[1]
+        else:
+            fp64 = derived
+            kind = "derived (%d SMs x %d FP64 FMA/clk x 2 flop x %.0f MHz); %s" % (
+                sms, FP64_FMA_PER_SM_CLK, mhz, fp64_peak[1] if fp64_peak else "not measured")
         achieved = flops / (dom_ms * 1e-3) / 1e12
         return {"bound": "alu", "pipe": "fp64", "kernel": dom["name"], "achieved": round(achieved, 4),
-                "peak": round(fp64_peak, 4),
-                "peak_kind": "derived (%d SMs x %d FP64 FMA/clk x 2 flop x %.0f MHz)" % (sms, FP64_FMA_PER_SM_CLK, mhz),
-                "unit": "TFLOP/s", "frac": round(achieved / fp64_peak, 4), "traffic": traffic,
+                "peak": round(fp64, 4), "peak_kind": kind, "derived_peak": round(derived, 4),
+                "unit": "TFLOP/s", "frac": round(achieved / fp64, 4), "traffic": traffic,
                 "algorithmic_flops": flops, "algorithmic_bytes": dom["bytes"], "launch_ms": round(dom_ms, 5),
                 "hbm": {"achieved": round(gbs, 1), "peak": peak, "peak_kind": peak_kind, "frac": round(gbs / peak, 4)}}
     return {"bound": "hbm", "kernel": dom["name"], "achieved": round(gbs, 1), "peak": peak,
@@ -129,21 +159,28 @@ def dominant_roofline(dom, dom_ms, peak, peak_kind, refined_iters, clocks):
 
 
 class ClockSampler:
-    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+    """nvidia-smi clocks and throttle reasons, sampled every 10 ms from before
+    the warm-up steps until after the timed region.  Every reading carries the
+    host time it arrived; the summary keeps the readings that arrived while
+    the timed region ran, and when the region is shorter than the sampling
+    period (a few dozen milliseconds) the last reading before it and the
+    first after it, taken while the warm-up steps and the timed steps kept
+    the GPU busy ("window": "bracketing")."""
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    PERIOD_MS = 10
 
     def __init__(self, index: int):
         self.index = index
         self.proc = None
-        self.lines = []
+        self.lines = []  # (host time, csv line)
 
     def start(self):
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
-                 "-lms", "50"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+                 "-lms", str(self.PERIOD_MS)], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.thread = threading.Thread(target=self._read, daemon=True)
             self.thread.start()
         except Exception:
@@ -154,36 +191,53 @@ class ClockSampler:
         t0 = time.time()
         while not self.lines and time.time() - t0 < 10.0:
             time.sleep(0.01)
-        self.lines.clear()
 
     def _read(self):
         for line in self.proc.stdout:
-            self.lines.append(line.strip())
+            self.lines.append((time.time(), line.strip()))
 
-    def stop(self):
+    @staticmethod
+    def _parse(line):
+        parts = [x.strip() for x in line.split(",")]
+        if len(parts) < 9:
+            return None
+        try:
+            sm, smax = float(parts[1]), float(parts[2])
+        except ValueError:
+            return None
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = {name for name, v in zip(names, parts[5:9]) if v.lower().startswith("active")}
+        return sm, smax, reasons
+
+    def stop(self, t_begin=None, t_end=None):
+        """Summary of the readings between host times t_begin and t_end."""
         if self.proc is None:
-            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+        time.sleep(2.5 * self.PERIOD_MS / 1e3)  # the first reading after the region
         self.proc.terminate()
         try:
             self.proc.wait(timeout=5)
         except Exception:
             self.proc.kill()
-        sm, smax, reasons = [], None, set()
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for line in self.lines:
-            parts = [x.strip() for x in line.split(",")]
-            if len(parts) < 9:
-                continue
-            try:
-                sm.append(float(parts[1]))
-                smax = float(parts[2])
-            except ValueError:
-                continue
-            for name, v in zip(names, parts[5:9]):
-                if v.lower().startswith("active"):
-                    reasons.add(name)
+        rows = [(t, r) for t, r in ((t, self._parse(line)) for t, line in list(self.lines)) if r is not None]
+        window = "timed region"
+        if t_begin is None:
+            chosen = rows
+        else:
+            chosen = [(t, r) for t, r in rows if t_begin <= t <= t_end]
+            if not chosen:
+                before = [(t, r) for t, r in rows if t < t_begin]
+                after = [(t, r) for t, r in rows if t > t_end]
+                chosen = before[-1:] + after[:1]
+                window = "bracketing"
+        sm = [r[0] for _, r in chosen]
+        smax = max((r[1] for _, r in chosen), default=None)
+        reasons = set()
+        for _, r in chosen:
+            reasons |= r[2]
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
-                "reasons": sorted(reasons), "samples": len(sm)}
+                "reasons": sorted(reasons), "samples": len(sm), "window": window,
+                "period_ms": self.PERIOD_MS, "readings_total": len(rows)}
 
 
 def dist_setup():
@@ -393,38 +447,36 @@ def run_ours(args):
             it["fn"]()
             e1.record(stream)
 
-    # every event of the timed region exists before it starts, and one
-    # warm-up step records events too, so no first-use cost lands in a timed
-    # launch
-    ev = make_events(args.steps)
-    step(make_events(1))
-    for _ in range(max(0, args.warmup - 1)):
-        step()
-    torch.cuda.synchronize()
-
     def barrier():
         if world > 1:
             import torch.distributed as dist
             dist.barrier()
         torch.cuda.synchronize()
 
-    # the clock sampler starts while the GPU is busy with two more warm-up
-    # steps, so the timed region never begins on a GPU that has been idle
+    # every event of the timed region exists before it starts, and the first
+    # warm-up step records events too, so no first-use cost lands in a timed
+    # launch.  The clock sampler runs from before the warm-up steps to after
+    # the timed region.
+    fp64_peak = measure_fp64_peak(torch) if "refined_%d" % REF_N in [it["name"] for it in wl.items] else None
+    ev = make_events(args.steps)
+    ev_warm = make_events(1)
     sampler = ClockSampler(local if world > 1 else 0)
     sampler.start()
-    for _ in range(2):
-        step()
+    for w in range(args.warmup):
+        step(ev_warm if w == 0 else None)
     barrier()
     t0 = torch.cuda.Event(enable_timing=True)
     t1 = torch.cuda.Event(enable_timing=True)
     torch.cuda.nvtx.range_push("timed")  # lets a profiler keep exactly the timed launches
+    host_begin = time.time()
     t0.record(stream)
     for k in range(args.steps):
         step(ev, k)
     t1.record(stream)
     torch.cuda.nvtx.range_pop()
     barrier()
-    clocks = sampler.stop()
+    host_end = time.time()
+    clocks = sampler.stop(host_begin, host_end)
     total_ms = max_over_ranks(t0.elapsed_time(t1), world, dev)
 
     per_item, per_item_median, per_item_pct = {}, {}, {}
@@ -451,7 +503,7 @@ def run_ours(args):
         refined_iters = {"mean": round(float(it_np.mean()), 3), "max": int(it_np.max()), "min": int(it_np.min())}
     # dominant kernel: the launch with the largest share of the step
     dom = max(wl.items, key=lambda it: per_item[it["name"]])
-    roofline = dominant_roofline(dom, per_item[dom["name"]], peak, peak_kind, refined_iters, clocks)
+    roofline = dominant_roofline(dom, per_item[dom["name"]], peak, peak_kind, refined_iters, clocks, fp64_peak)
     step_ms = total_ms / args.steps
     value = job_value(world, wl.elems, step_ms)
     launches_per_step = len(wl.items)

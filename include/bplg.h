@@ -23,7 +23,12 @@
  *     memory.  Compute entry points never allocate on their hot path; the
  *     first FFT call on a device allocates the shared twiddle table (256 KB)
  *     once, synchronously, so it must not be the first call inside a stream
- *     capture.
+ *     capture.  The library keeps such per-device state (tables, scratch,
+ *     kernel attributes) for the life of the process: do not use it on a
+ *     device after cudaDeviceReset of that device.
+ *   - Grid: a call whose batch would need more than 2^31 - 1 blocks under its
+ *     plan (problems per block) returns BPLG_ERR_UNSUPPORTED_SIZE before
+ *     anything is enqueued.
  *   - Layout: batched data is row-major [batch][n], problem after problem,
  *     with no padding between problems.  Device pointers must be 16-byte
  *     aligned.
@@ -184,11 +189,13 @@ int bplg_fft_batched(const void *in, void *out, int64_t n, int64_t batch, int32_
                      const bplg_plan *plan, void *stream);
 
 /* The same FFT with every radix-16 Stockham stage run on tensor cores: each
- * 16-point DFT of a stage is a 32 x 32 real contraction (mma.sync
- * m16n8k16) on 16-bit operands split into hi and lo parts, x = xh + xl and
- * F = Fh + Fl, summing xh Fh + xh Fl + xl Fh in float32; twiddles are
- * applied in float32 from the float64-generated table, and a mixed-radix
- * first stage (log2 n not a multiple of 4) runs on the CUDA cores.  Not in
+ * 16-point DFT of a stage is a 32 x 32 real contraction on 16-bit operands
+ * split into hi and lo parts, x = xh + xl and F = Fh + Fl, summing
+ * xh Fh + xh Fl + xl Fh in float32.  Plan io 0 (the default) issues the
+ * contractions as tcgen05.mma with the accumulator in tensor memory (n >=
+ * 1024); io 1 is the legacy mma.sync m16n8k16 form.  Twiddles are applied in
+ * float32 from the float64-generated table, and a mixed-radix first stage
+ * (log2 n not a multiple of 4) runs on the CUDA cores.  Not in
  * the paper (whose FFT is float32 on CUDA cores, Section III); the error
  * against the float64 oracle is reported per size.
  *   precision BPLG_TC_BF16 or BPLG_TC_F16 (FP16 scales each stage by 1/4,
@@ -213,15 +220,18 @@ int bplg_fft_tc_batched(const void *in, void *out, int64_t n, int64_t batch, int
  *   in,out  device, [batch][n] complex64 interleaved; in == out is allowed.
  *   dir     -1 forward, +1 inverse (unnormalised).
  *   plan    a valid FFT plan with io 0 or 1, or NULL for a fixed default
- *           (radix min(16, n), at least 128 threads per block).
- * Set-up: the first call on each device, with that device current, looks up
- * the array's device address (cudaGetSymbolAddress) and fills the table on
- * `stream`, waiting for it before returning; make that first call before any
- * stream capture.  All calls share the array.  It is written only by that
- * set-up and only read afterwards, so nothing in it has to start at zero and
- * calls that overlap each other on the GPU read it concurrently without
- * harm; a call that overlapped the set-up would race with it, which is why
- * the set-up completes before the first call returns.
+ *           (radix min(16, n), at least 128 threads per block).  A plan whose
+ *           shared memory exceeds the device's per-block limit returns
+ *           BPLG_ERR_INVALID_PLAN.
+ * Set-up: the table's values are a static initializer of the array (made at
+ * build time in float64 and rounded once to float32), so they are in place
+ * as soon as the library's code is loaded on a device; nothing is launched
+ * or waited for.  The first call on each device, with that device current,
+ * looks up the array's device address (cudaGetSymbolAddress), which can load
+ * the library's code on that device; make that first call before any stream
+ * capture.  All calls share the array, which is only ever read, so nothing in
+ * it has to start at zero and calls that overlap each other on the GPU read
+ * it concurrently without harm.
  * Errors: INVALID_ARG, UNSUPPORTED_SIZE, INVALID_PLAN, CUDA. */
 int bplg_fft_batched_noalloc(const void *in, void *out, int64_t n, int64_t batch, int32_t dir,
                              const bplg_plan *plan, void *stream);
@@ -387,10 +397,12 @@ typedef struct {
  * with a_j = (op, dtype, n, batch), where f is the median time of timed
  * launches on the current device on library-owned buffers of that shape.
  *   ANALYTIC    the guideline on the device limits; no GPU evaluation.
- *   LEARNED     Bayesian optimisation: seeded random initial samples, a
- *               Gaussian-process surrogate (Matern-5/2 on the encoded knobs,
- *               on log time), expected improvement, stop after 5 evaluations
- *               without improvement or at `budget` evaluations.
+ *   LEARNED     Bayesian optimisation: a seeded space-filling initial
+ *               design, a Gaussian-process surrogate (Matern-5/2 on the
+ *               encoded knobs, on log time), expected improvement, stop after
+ *               a window of 8 evaluations without improvement (environment
+ *               variable BPLG_BO_WINDOW = 1..64 overrides it; 5 is the
+ *               paper's) or at `budget` evaluations (0 = 40).
  *   EXHAUSTIVE  every valid plan is timed.
  * The result is stored in the per-process plan cache that bplg_query_plan
  * reads.  Synchronous.  Errors: INVALID_ARG, UNSUPPORTED_SIZE, CUDA, NO_DEVICE. */

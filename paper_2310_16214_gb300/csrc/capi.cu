@@ -1,4 +1,5 @@
 // extern "C" entry points: argument validation, plan resolution, dispatch.
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <functional>
@@ -37,11 +38,27 @@ namespace {
 std::mutex g_default_mu;
 std::map<std::tuple<int, int, int, int64_t>, bplg_plan> g_default;  // (device, op, dtype, n)
 
+// Blocks the launch of a caller's plan would need, from the plan alone (no
+// device query): one block per spb problems, or for the two-kernel FFT the
+// larger of its two grids.  Saturates at kMaxGridBlocks + 1.
+int64_t plan_blocks(const bplg_plan &p, int64_t n, int64_t batch) {
+    if (p.op == BPLG_OP_FFT && n > (int64_t(1) << kFftMaxLog) && p.n1_log > 0 && p.n1_log < 31) {
+        // at least one block per signal in each kernel
+        if (batch > kMaxGridBlocks) return kMaxGridBlocks + 1;
+        const int64_t n1 = int64_t(1) << p.n1_log, n2 = n / n1;
+        const int64_t cols = p.spb > 0 ? batch * std::max<int64_t>(1, n2 / p.spb) : 0;
+        const int64_t rows = p.row_spb > 0 ? batch * std::max<int64_t>(1, n1 / p.row_spb) : 0;
+        return std::max(cols, rows);
+    }
+    return p.spb > 0 ? batch / p.spb + (batch % p.spb != 0 ? 1 : 0) : 0;
+}
+
 int resolve_plan(int op, int dtype, int64_t n, int64_t batch, const bplg_plan *given, bplg_plan *out,
                  OnlineTicket *ticket = nullptr) {
     if (given) {
         bplg_plan p = *given;
         if (p.op != op) return set_error(BPLG_ERR_INVALID_PLAN, "plan is for another operation");
+        if (p.spb >= 1 && plan_blocks(p, n, batch) > kMaxGridBlocks) return check_grid(plan_blocks(p, n, batch), "plan");
         std::string why;
         int rc = check_plan_on_device(p, dtype, n, &why);
         if (rc == BPLG_ERR_INVALID_PLAN) return set_error(rc, "invalid plan: " + why);

@@ -725,8 +725,10 @@ int fft_launch(const bplg_plan &p, const void *in, void *out, int64_t n, int64_t
     if (n > (int64_t(1) << kFftMaxLog)) return fft_large_launch(p, in, out, n, batch, dir, s);
     Launch li;
     if (!fft_launch_info(p, n, batch, dir, &li)) return set_error(BPLG_ERR_INVALID_PLAN, "fft: plan has no kernel");
+    int rc = check_grid(li.blocks, "fft");
+    if (rc != BPLG_OK) return rc;
     const void *tw = nullptr;
-    int rc = twiddles_for_current_device(&tw);
+    rc = twiddles_for_current_device(&tw);
     if (rc != BPLG_OK) return rc;
     rc = ensure_smem_attr(li.func, li.smem);
     if (rc != BPLG_OK) return rc;
@@ -791,37 +793,35 @@ constexpr int kNoAllocMaxDevices = 64;
 
 }  // namespace bplg
 
-// W_M^k at [M + k] for M = 2 .. kNoAllocMaxN, as in the regular table
-static __device__ __align__(256) float2 g_noalloc_twiddles[2 * bplg::kNoAllocMaxN];
+// W_M^k at [M + k] for M = 2 .. kNoAllocMaxN, as in the regular table.  The
+// values are part of the module image (a static initializer written at build
+// time from float64 values rounded once to float32), so the array is ready
+// as soon as the module is loaded on a device: no fill kernel, no wait, and a
+// module reloaded after cudaDeviceReset holds them again.
+static __device__ __align__(256) float2 g_noalloc_twiddles[2 * bplg::kNoAllocMaxN] = {
+#include "noalloc_twiddles.inc"
+};
 
 namespace bplg {
 namespace {
 
 std::mutex g_noalloc_mu;
-float2 *g_noalloc_addr[kNoAllocMaxDevices];  // device address of the array, per device
-bool g_noalloc_ready[kNoAllocMaxDevices];
+const float2 *g_noalloc_addr[kNoAllocMaxDevices];  // device address of the array, per device
 
 // Set-up, once per device, with that device current: look up the array's
-// device address (the host-side name is only a stand-in for it) and fill it
-// with float64-generated twiddles.  The fill runs on the caller's stream and
-// is waited for before the first call returns.
-int noalloc_setup(cudaStream_t s, const float2 **tw) {
+// device address (in host code its name is only a stand-in for it, which a
+// kernel must never be given).  Nothing is launched or waited for.
+int noalloc_setup(const float2 **tw) {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return cuda_error(e, "cudaGetDevice");
     if (dev < 0 || dev >= kNoAllocMaxDevices) return set_error(BPLG_ERR_INVALID_ARG, "device index too large");
     std::lock_guard<std::mutex> lock(g_noalloc_mu);
-    if (!g_noalloc_ready[dev]) {
+    if (!g_noalloc_addr[dev]) {
         float2 *ptr = nullptr;
         e = cudaGetSymbolAddress(reinterpret_cast<void **>(&ptr), g_noalloc_twiddles);
         if (e != cudaSuccess) return cuda_error(e, "cudaGetSymbolAddress(no-alloc twiddles)");
-        const int total = 2 * kNoAllocMaxN;
-        twiddle_init_kernel<<<(total + 255) / 256, 256, 0, s>>>(ptr, kNoAllocMaxLog);
-        e = cudaGetLastError();
-        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-        if (e != cudaSuccess) return cuda_error(e, "no-alloc twiddle set-up");
         g_noalloc_addr[dev] = ptr;
-        g_noalloc_ready[dev] = true;
     }
     *tw = g_noalloc_addr[dev];
     return BPLG_OK;
@@ -865,21 +865,30 @@ extern "C" int bplg_fft_batched_noalloc(const void *in, void *out, int64_t n, in
     const void *func = fft_func(p.radix, dir, p.smem_layout, p.smem_pad, p.io, p.L, ilog2(n));
     if (!func) return set_error(BPLG_ERR_INVALID_PLAN, "fft no-alloc: plan has no kernel");
     const int smem = fft_smem_bytes(p.radix, p.smem_layout, p.smem_pad, p.io, n, p.spb);
+    const int64_t blocks = batch / p.spb + (batch % p.spb != 0 ? 1 : 0);
+    int rc = check_grid(blocks, "fft no-alloc");
+    if (rc != BPLG_OK) return rc;
+    int dev = 0, optin = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_error(e, "cudaGetDevice");
+    e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (e != cudaSuccess) return cuda_error(e, "cudaDeviceGetAttribute");
     cudaFuncAttributes fa;
-    cudaError_t e = cudaFuncGetAttributes(&fa, func);
+    e = cudaFuncGetAttributes(&fa, func);
     if (e != cudaSuccess) return cuda_error(e, "cudaFuncGetAttributes");
     if (p.L > fa.maxThreadsPerBlock) return set_error(BPLG_ERR_INVALID_PLAN, "fft no-alloc: block too large for the kernel");
+    if (static_cast<int64_t>(smem) + static_cast<int64_t>(fa.sharedSizeBytes) > optin)
+        return set_error(BPLG_ERR_INVALID_PLAN, "fft no-alloc: the plan's shared memory is above the per-block limit");
     if (smem > fa.maxDynamicSharedSizeBytes) {
         e = cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         if (e != cudaSuccess) return cuda_error(e, "cudaFuncSetAttribute(max dynamic smem)");
     }
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const float2 *tw = nullptr;
-    int rc = noalloc_setup(s, &tw);
+    rc = noalloc_setup(&tw);
     if (rc != BPLG_OK) return rc;
     int logn = ilog2(n);
     int spb = p.spb;
-    const int64_t blocks = (batch + spb - 1) / spb;
     void *args[] = {(void *)&in, (void *)&out, (void *)&tw, &logn, &spb, &batch};
     e = cudaLaunchKernel(func, dim3(static_cast<unsigned>(blocks)), dim3(p.L), args, static_cast<size_t>(smem), s);
     return e == cudaSuccess ? BPLG_OK : cuda_error(e, "fft no-alloc launch");

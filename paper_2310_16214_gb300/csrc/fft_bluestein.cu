@@ -241,6 +241,8 @@ int fft_bluestein_launch(const bplg_plan *plan_m, const void *in, void *out, int
         rc = ensure_smem_attr(f, smem);
         if (rc != BPLG_OK) return rc;
         const int64_t blocks = (batch + spb - 1) / spb;
+        rc = check_grid(blocks, "fft (Bluestein)");
+        if (rc != BPLG_OK) return rc;
         const float2 *xi = static_cast<const float2 *>(in);
         float2 *xo = static_cast<float2 *>(out);
         void *args[] = {(void *)&xi, (void *)&xo, (void *)&t.h, (void *)&t.G, (void *)&tw, &n, &spb, &batch};

@@ -314,9 +314,10 @@ int fft_large_launch(const bplg_plan &p, const void *in, void *out, int64_t n, i
     Launch l0, l1;
     if (!fft_large_launch_info(p, n, batch, dir, 0, &l0) || !fft_large_launch_info(p, n, batch, dir, 1, &l1))
         return set_error(BPLG_ERR_INVALID_PLAN, "fft (two kernels): plan has no kernel");
-    if (l0.blocks > 0x7FFFFFFF || l1.blocks > 0x7FFFFFFF) return set_error(BPLG_ERR_INVALID_ARG, "fft: batch too large");
+    int rc = check_grid(l0.blocks > l1.blocks ? l0.blocks : l1.blocks, "fft (two kernels)");
+    if (rc != BPLG_OK) return rc;
     const void *tw = nullptr;
-    int rc = twiddles_for_current_device(&tw);
+    rc = twiddles_for_current_device(&tw);
     if (rc != BPLG_OK) return rc;
     int logn = ilog2(n);
     const float2 *fine = nullptr;

@@ -546,8 +546,10 @@ int fft_tc_launch(const bplg_plan &p, const void *in, void *out, int64_t n, int6
     Launch li;
     if (!fft_tc_launch_info(p, n, batch, prec, dir, &li))
         return set_error(BPLG_ERR_INVALID_PLAN, "fft tc: plan has no kernel");
+    int rc = check_grid(li.blocks, "fft tc");
+    if (rc != BPLG_OK) return rc;
     const void *tw = nullptr;
-    int rc = twiddles_for_current_device(&tw);
+    rc = twiddles_for_current_device(&tw);
     if (rc != BPLG_OK) return rc;
     rc = ensure_smem_attr(li.func, li.smem);
     if (rc != BPLG_OK) return rc;

@@ -46,6 +46,13 @@ constexpr int kFftLargeMaxLog = 24;  // two-kernel transforms beyond that
 constexpr int kTridiagMaxLog = 13;
 constexpr int kRefinedMaxLog = 12;
 
+// Largest grid (x dimension) of one launch: 2^31 - 1 blocks.
+constexpr int64_t kMaxGridBlocks = 2147483647;
+// BPLG_OK, or BPLG_ERR_UNSUPPORTED_SIZE (with a message naming `what`) when
+// a launch would need more than kMaxGridBlocks blocks (batch too large for
+// the plan's problems per block)
+int check_grid(int64_t blocks, const char *what);
+
 // ---- per-op kernel tables (each returns false if the plan has no kernel)
 bool scan_launch_info(const bplg_plan &p, int dtype, int64_t n, int64_t batch, Launch *out);
 int scan_launch(const bplg_plan &p, int dtype, const void *in, void *out, int64_t n, int64_t batch,

@@ -40,6 +40,15 @@ int cuda_error(cudaError_t e, const char *what) {
 
 void clear_error() { t_last_error.clear(); }
 
+int check_grid(int64_t blocks, const char *what) {
+    if (blocks >= 1 && blocks <= kMaxGridBlocks) return BPLG_OK;
+    char buf[256];
+    std::snprintf(buf, sizeof(buf),
+                  "%s: the batch needs %lld blocks, above the grid limit of 2^31 - 1; split the batch or use a plan "
+                  "with more problems per block", what, static_cast<long long>(blocks));
+    return set_error(BPLG_ERR_UNSUPPORTED_SIZE, buf);
+}
+
 int launch_error(cudaError_t e, const char *what, const void *func, int64_t grid, int threads, int smem) {
     char buf[512];
     cudaFuncAttributes fa;

@@ -157,6 +157,8 @@ int scan_launch(const bplg_plan &p, int dtype, const void *in, void *out, int64_
     Launch li;
     if (!scan_launch_info(p, dtype, np, batch, &li)) return set_error(BPLG_ERR_INVALID_PLAN, "scan: plan has no kernel");
     if (np != n) li.func = scan_func(dtype, p.P, p.pattern, true);
+    int rc = check_grid(li.blocks, "scan");
+    if (rc != BPLG_OK) return rc;
     int log_t = ilog2(np / p.P);
     int spb = p.spb;
     void *args[] = {const_cast<void **>(&in), &out, &log_t, &spb, &batch, &n};

@@ -1189,7 +1189,9 @@ int tridiag_launch(const bplg_plan &p, const float *a, const float *b, const flo
     Launch li;
     if (!tridiag_launch_info(p, n, batch, false, &li))
         return set_error(BPLG_ERR_INVALID_PLAN, "tridiag: plan has no kernel");
-    int rc = ensure_smem_attr(li.func, li.smem);
+    int rc = check_grid(li.blocks, "tridiag");
+    if (rc != BPLG_OK) return rc;
+    rc = ensure_smem_attr(li.func, li.smem);
     if (rc != BPLG_OK) return rc;
     int logn = ilog2(n), log_m = ilog2(p.cr_switch), log_tps = ilog2(n / p.P), spb = p.spb;
     if (p.io == 1) {
@@ -1218,7 +1220,9 @@ int tridiag_refined_launch(const bplg_plan &p, const float *a, const float *b, c
     Launch li;
     if (!tridiag_launch_info(p, n, batch, true, &li))
         return set_error(BPLG_ERR_INVALID_PLAN, "tridiag refined: plan has no kernel");
-    int rc = ensure_smem_attr(li.func, li.smem);
+    int rc = check_grid(li.blocks, "refined");
+    if (rc != BPLG_OK) return rc;
+    rc = ensure_smem_attr(li.func, li.smem);
     if (rc != BPLG_OK) return rc;
     int logn = ilog2(n), log_m = ilog2(p.cr_switch), log_tps = ilog2(n / p.P), spb = p.spb;
     void *args[] = {(void *)&a,    (void *)&b,  (void *)&c,     (void *)&d,  (void *)&x,      (void *)&iters, &logn,

@@ -168,7 +168,9 @@ int tridiag_wm_launch(const bplg_plan &p, const float *a, const float *b, const 
     if (!tridiag_wm_launch_info(p, np, batch, &li))
         return set_error(BPLG_ERR_INVALID_PLAN, "tridiag (Wang-Mou): plan has no kernel");
     if (np != n) li.func = wm_func<true>(p.P, p.radix, p.shuffle);
-    int rc = ensure_smem_attr(li.func, li.smem);
+    int rc = check_grid(li.blocks, "tridiag (Wang-Mou)");
+    if (rc != BPLG_OK) return rc;
+    rc = ensure_smem_attr(li.func, li.smem);
     if (rc != BPLG_OK) return rc;
     int logn = ilog2(np), log_tps = ilog2(np / p.P), spb = p.spb, nrow = static_cast<int>(n);
     void *args[] = {(void *)&a, (void *)&b, (void *)&c, (void *)&d, (void *)&x, &logn, &log_tps, &spb, &batch, &nrow};

@@ -240,3 +240,27 @@ def test_no_device_is_reported_not_faked():
         pass
     rc = bp.lib.bplg_scan_batched(0, 4096, 4096, 64, 1, None, None)
     assert rc == bp.ERR_NO_DEVICE
+
+
+def test_grid_above_the_launch_limit_is_rejected_before_any_device_call():
+    """A batch that would need more than 2^31 - 1 blocks under the caller's
+    plan is refused on the host (nothing is enqueued); one block fewer gets
+    past that check (and then, on a machine without a GPU, stops at the
+    device query)."""
+    try:
+        import torch
+        if torch.cuda.is_available():
+            pytest.skip("a GPU is present: the just-below-the-limit calls would reach it")
+    except ImportError:
+        pass
+    import ctypes
+    P = bp.lib
+    scan = bp.make_plan(bp.OP_SCAN, 32, P=1, spb=1)  # one 32-element problem per block
+    assert P.bplg_scan_batched(0, 16, 16, 32, 1 << 31, ctypes.byref(scan), None) == bp.ERR_UNSUPPORTED_SIZE
+    assert "2^31" in bp.last_error()
+    assert P.bplg_scan_batched(0, 16, 16, 32, (1 << 31) - 1, ctypes.byref(scan), None) == bp.ERR_NO_DEVICE
+    fft = bp.make_plan(bp.OP_FFT, 64, P=2, spb=1)
+    assert P.bplg_fft_batched(16, 16, 64, 1 << 31, -1, ctypes.byref(fft), None) == bp.ERR_UNSUPPORTED_SIZE
+    assert P.bplg_fft_batched_noalloc(16, 16, 64, 1 << 31, -1, ctypes.byref(fft), None) == bp.ERR_UNSUPPORTED_SIZE
+    tri = bp.make_plan(bp.OP_TRIDIAG, 64, P=2, spb=1, cr_switch=32, shuffle=1)
+    assert P.bplg_tridiag_batched(16, 16, 16, 16, 16, 64, 1 << 33, ctypes.byref(tri), None) == bp.ERR_UNSUPPORTED_SIZE

@@ -178,3 +178,22 @@ def test_argument_errors(bp):
 def test_no_device_error_recorded(bp):
     # every pipelined launch above completed its bounded waits
     assert bp.device_status() == 0
+
+
+@pytest.mark.parametrize("scale_log2", [100, -100])
+def test_systems_scaled_by_powers_of_two(bp, scale_log2):
+    """A system multiplied through by 2^100 or 2^-100 (exactly, every
+    coefficient and right-hand side) has the same solution: the CR/PCR and
+    Wang-Mou solves and the refined solve keep their tolerances at both ends
+    of the float32 range the pivots may take."""
+    n, batch = 1024, 6
+    a, b, c, d, _ = si.tridiag_f32(batch, n, stream=11)
+    ref = oracle.thomas(a, b, c, d)
+    s = np.float32(2.0 ** scale_log2)
+    scaled = tuple(v * s for v in (a, b, c, d))
+    assert np.array_equal(oracle.thomas(*scaled), ref)
+    assert tri_rel_err(run_tri(bp, scaled), ref).max() <= 1e-4
+    wm = bp.query_plan(bp.OP_TRIDIAG_WM, bp.F32, n, batch)
+    assert tri_rel_err(run_tri(bp, scaled, wm), ref).max() <= 1e-4
+    x, _ = run_refined(bp, scaled, tol=1e-14)
+    assert tri_rel_err(x, ref).max() <= 1e-12

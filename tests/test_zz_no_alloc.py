@@ -82,3 +82,39 @@ def test_noalloc_rejects_sizes_beyond_its_table(bp):
     rc = bp.lib.bplg_fft_batched_noalloc(v.data_ptr(), v.data_ptr(), 8192, 1, -1, None, None)
     assert rc == bp.ERR_UNSUPPORTED_SIZE
     assert "4096" in bp.last_error()
+
+
+@pytest.mark.parametrize("n", [16, 1024, 4096])
+def test_noalloc_against_the_oracle(bp, n):
+    """Checked directly against the float64 oracle as well, both directions."""
+    import oracle
+    batch = 23
+    z = si.fft_c64(batch, n, stream=940 + n)
+    zin = _c64(z)
+    stream = torch.cuda.current_stream().cuda_stream
+    for direction in (-1, +1):
+        out = torch.full_like(zin, float("nan"))
+        rc = bp.lib.bplg_fft_batched_noalloc(zin.data_ptr(), out.data_ptr(), n, batch, direction, None, stream)
+        assert rc == 0, bp.last_error()
+        torch.cuda.synchronize()
+        X = out.cpu().numpy().view(np.complex64).reshape(batch, n).astype(np.complex128)
+        ref = oracle.fft(z, direction)
+        err = np.linalg.norm(X - ref, axis=-1) / np.linalg.norm(ref, axis=-1)
+        assert err.max() <= 1e-5 * math.log2(n), (direction, err.max())
+
+
+@pytest.mark.parametrize("n", [16, 4096])
+def test_noalloc_in_place(bp, n):
+    """out == in, which the entry point allows."""
+    import oracle
+    batch = 9
+    z = si.fft_c64(batch, n, stream=960 + n)
+    buf = _c64(z)
+    stream = torch.cuda.current_stream().cuda_stream
+    rc = bp.lib.bplg_fft_batched_noalloc(buf.data_ptr(), buf.data_ptr(), n, batch, -1, None, stream)
+    assert rc == 0, bp.last_error()
+    torch.cuda.synchronize()
+    X = buf.cpu().numpy().view(np.complex64).reshape(batch, n).astype(np.complex128)
+    ref = oracle.fft(z, -1)
+    assert (np.linalg.norm(X - ref, axis=-1) / np.linalg.norm(ref, axis=-1)).max() <= 1e-5 * math.log2(n)
+
