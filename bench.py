@@ -280,6 +280,7 @@ class Workload:
         self.fixed = plan_json or {}
         self.seed = seed
         self.tuning = {"mode": plans, "seconds": 0.0, "evaluations": 0}
+        self.learned = {}  # row -> (plan, BO evaluations, space size)
         t = torch
         for n in FFT_SIZES:
             batch = max(1, int(FFT_TOTAL * scale) // n)
@@ -406,6 +407,7 @@ class Workload:
         p, rep = bp.tune_plan(op, dtype, n, batch, bp.TUNE_LEARNED, budget=40, seed=self.seed)
         self.tuning["seconds"] += time.time() - t0
         self.tuning["evaluations"] += rep.evaluations
+        self.learned[name] = (p, rep.evaluations, rep.space_size)
         return p
 
     def _add(self, name, op, n, batch, elems, nbytes, fn, ins, outs, plan):
@@ -529,6 +531,12 @@ def run_ours(args):
             ext = {"unavailable": str(exc)[:200]}
     e2e = measure_e2e(torch, wl, stream, args) if rank == 0 and not args.no_e2e else None
     cpu = cpu_baseline(args) if (rank == 0 and world == 1 and not args.no_cpu) else None
+    tuning = None
+    if rank == 0 and not args.no_tuning and args.plans == "learned" and wl.learned:
+        try:
+            tuning = tuning_quality(bp, wl)
+        except Exception as exc:  # reported, never fatal to the bench line
+            tuning = {"unavailable": str(exc)[:200]}
 
     if rank == 0:
         line = {
@@ -543,12 +551,72 @@ def run_ours(args):
                        "parallelism": "replicas" if world > 1 else "single"},
             "roofline": roofline, "per_op": per_op, "per_launch": items_out,
             "gpu_launches": launches_per_step * args.steps, "clocks": clocks, "refined_corrections": refined_iters,
-            "e2e": e2e, "cpu_baseline": cpu, "external": ext,
+            "e2e": e2e, "cpu_baseline": cpu, "external": ext, "tuning": tuning,
         }
         print(json.dumps(line))
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
+
+
+def tuning_quality(bp, wl, reps: int = 30):
+    """Tuned vs exhaustive-best (Section VI) for every op and size of the
+    timed step (forward FFTs, CR/PCR solves, the refined solve, both scans):
+    the plan of the GB300 cost model (BPLG_TUNE_MODEL, no evaluation), of the
+    paper's guideline (BPLG_TUNE_ANALYTIC, no evaluation), of the learned
+    tuner the step runs with (Bayesian optimisation), and of exhaustive search
+    over the same space, re-timed back to back by bplg_time_plan (median of
+    `reps` launches each, on library-owned buffers of the row's shape).
+    e = t_best / t_plan with t_best the fastest of the four; Phi per op is
+    the harmonic mean of e over its sizes."""
+    kinds = {"fft": (bp.OP_FFT, bp.F32), "tridiag": (bp.OP_TRIDIAG, bp.F32),
+             "refined": (bp.OP_TRIDIAG_REFINED, bp.F32), "scan_i32": (bp.OP_SCAN, bp.I32),
+             "scan_f32": (bp.OP_SCAN, bp.F32)}
+    t0 = time.time()
+    rows, exh_evals = [], 0
+    for it in wl.items:
+        name, op_name = it["name"], it["op"]
+        if op_name == "fft" and name.startswith("fft_inv"):
+            continue  # the tuners time forward transforms
+        if op_name not in kinds or name not in wl.learned:
+            continue
+        op, dt = kinds[op_name]
+        n, batch = it["n"], it["batch"]
+        pl, bo_evals, space = wl.learned[name]
+        pm, _ = bp.tune_plan(op, dt, n, batch, bp.TUNE_MODEL)
+        pg, _ = bp.tune_plan(op, dt, n, batch, bp.TUNE_ANALYTIC)
+        pe, rep_e = bp.tune_plan(op, dt, n, batch, bp.TUNE_EXHAUSTIVE)
+        exh_evals += rep_e.evaluations
+        times = {}
+        for key, p in (("model", pm), ("analytic", pg), ("learned", pl), ("exhaustive", pe)):
+            same = [k for k, q in (("model", pm), ("analytic", pg), ("learned", pl), ("exhaustive", pe))
+                    if k in times and q.key() == p.key()]
+            times[key] = times[same[0]] if same else bp.time_plan(p, dt, n, batch, reps)
+        best = min(times.values())
+        rows.append({"row": name, "op": op_name, "n": n, "batch": batch, "space": space,
+                     "bo_evaluations": bo_evals,
+                     "ms": {k: round(v, 5) for k, v in times.items()},
+                     "e": {k: round(best / v, 4) for k, v in times.items() if k != "exhaustive"}})
+    per_op = {}
+    for o in kinds:
+        rs = [r for r in rows if r["op"] == o]
+        if not rs:
+            continue
+        per_op[o] = {k: round(bp.phi([r["e"][k] for r in rs]), 4) for k in ("model", "analytic", "learned")}
+        per_op[o]["sizes"] = [r["n"] for r in rs]
+        per_op[o]["bo_evaluations"] = [r["bo_evaluations"] for r in rs]
+        per_op[o]["space"] = [r["space"] for r in rs]
+    allrows = rows
+    return {"phi": per_op,
+            "phi_all": {k: round(bp.phi([r["e"][k] for r in allrows]), 4) for k in ("model", "analytic", "learned")}
+            if allrows else None,
+            "rows": rows, "exhaustive_evaluations": exh_evals, "reps": reps,
+            "seconds": round(time.time() - t0, 1),
+            "method": "each plan re-timed by bplg_time_plan (median of %d launches, library-owned buffers of the "
+                      "row's shape); e = fastest of the four / plan; Phi = harmonic mean over sizes (Section VI); "
+                      "model = BPLG_TUNE_MODEL (GB300 cost model, 0 evaluations), analytic = the paper's guideline "
+                      "(0 evaluations), learned = the plans the timed step ran (Bayesian optimisation, budget 40)"
+                      % reps}
 
 
 def external_refs(torch, per_item, peak, reps: int = 20):
@@ -861,14 +929,17 @@ def tune_report(args):
     for name, op, dt, n, batch, bpe in cases:
         t0 = time.time()
         pa, _ = bp.tune_plan(op, dt, n, batch, bp.TUNE_ANALYTIC)
+        pm, _ = bp.tune_plan(op, dt, n, batch, bp.TUNE_MODEL)
         pl, rl = bp.tune_plan(op, dt, n, batch, bp.TUNE_LEARNED, budget=args.bo_budget, seed=args.seed)
         pe, re_ = bp.tune_plan(op, dt, n, batch, bp.TUNE_EXHAUSTIVE)
         ta = bp.time_plan(pa, dt, n, batch, args.reps)
+        tm = bp.time_plan(pm, dt, n, batch, args.reps)
         tl = bp.time_plan(pl, dt, n, batch, args.reps)
         te = bp.time_plan(pe, dt, n, batch, args.reps)
-        best = min(ta, tl, te)
+        best = min(ta, tm, tl, te)
         row = {"op": name, "n": n, "batch": batch, "space": re_.space_size,
                "analytic": {"plan": pa.as_dict(), "ms": round(ta, 5), "e": round(best / ta, 4)},
+               "model": {"plan": pm.as_dict(), "ms": round(tm, 5), "e": round(best / tm, 4)},
                "learned": {"plan": pl.as_dict(), "ms": round(tl, 5), "e": round(best / tl, 4),
                            "evaluations": rl.evaluations},
                "exhaustive": {"plan": pe.as_dict(), "ms": round(te, 5), "evaluations": re_.evaluations},
@@ -882,6 +953,7 @@ def tune_report(args):
     for o in ops:
         rs = [r for r in rows if r["op"] == o]
         summary[o] = {"phi_analytic": round(bp.phi([r["analytic"]["e"] for r in rs]), 4),
+                      "phi_model": round(bp.phi([r["model"]["e"] for r in rs]), 4),
                       "phi_learned": round(bp.phi([r["learned"]["e"] for r in rs]), 4),
                       "bo_evaluations": [r["learned"]["evaluations"] for r in rs],
                       "space": [r["space"] for r in rs]}
@@ -1145,6 +1217,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-ext", action="store_true", help="skip the cuFFT / CUB / cuSPARSE references")
+    ap.add_argument("--no-tuning", action="store_true",
+                    help="skip the tuned-vs-exhaustive (Phi) measurement after the timed region")
     ap.add_argument("--tune-report", action="store_true", help="tuned vs exhaustive Phi report instead of the bench")
     ap.add_argument("--precision-report", action="store_true",
                     help="tensor-core (BF16/FP16 split) vs float32 FFT: error and time per N")

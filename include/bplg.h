@@ -73,7 +73,12 @@ typedef enum {
 } bplg_op;
 
 typedef enum { BPLG_PATTERN_KS = 0, BPLG_PATTERN_LF = 1 } bplg_scan_pattern;
-typedef enum { BPLG_TUNE_ANALYTIC = 0, BPLG_TUNE_LEARNED = 1, BPLG_TUNE_EXHAUSTIVE = 2 } bplg_tune_method;
+typedef enum {
+    BPLG_TUNE_ANALYTIC = 0,   /* Section IV-A guideline, as the paper states it (Maxwell-era thresholds) */
+    BPLG_TUNE_LEARNED = 1,    /* Section IV-B Bayesian optimisation over timed candidates */
+    BPLG_TUNE_EXHAUSTIVE = 2, /* every valid plan timed (Section VI's reference) */
+    BPLG_TUNE_MODEL = 3       /* Section IV-A premises restated as a GB300 cost model; no evaluation */
+} bplg_tune_method;
 typedef enum { BPLG_TC_BF16 = 0, BPLG_TC_F16 = 1 } bplg_tc_precision;
 
 /* --------------------------------------------------------------- the plan
@@ -396,7 +401,20 @@ typedef struct {
 /* The tuning problem of Section IV-B: argmin over the plans x_B of f(a_j, x_B)
  * with a_j = (op, dtype, n, batch), where f is the median time of timed
  * launches on the current device on library-owned buffers of that shape.
- *   ANALYTIC    the guideline on the device limits; no GPU evaluation.
+ *   ANALYTIC    the guideline of Section IV-A on the device limits, as the
+ *               paper states it (its occupancy thresholds were set for a
+ *               Maxwell SM); no GPU evaluation.
+ *   MODEL       the premises of Section IV-A (coalescing, occupancy, ILP and
+ *               radix, kernel count) restated as a cost estimate for this GPU:
+ *               per plan, from the kernel's real register and shared-memory
+ *               counts and the device's SM count, clock and HBM bandwidth,
+ *               the soft maximum of the HBM time, the latency time (Little's
+ *               law: resident blocks each living one HBM round trip plus its
+ *               own transfer and compute), the issue time (instructions per
+ *               element of the op's algorithm), the load/store-unit time (128-
+ *               byte lines per warp-wide access), the block-launch time and,
+ *               for the refined solve, the FP64-pipe time; the plan with the
+ *               least estimate wins.  No GPU evaluation.
  *   LEARNED     Bayesian optimisation: a seeded space-filling initial
  *               design, a Gaussian-process surrogate (Matern-5/2 on the
  *               encoded knobs, on log time), expected improvement, stop after
@@ -411,8 +429,10 @@ int bplg_tune_plan(int32_t op, int32_t dtype, int64_t n, int64_t batch, int32_t 
 
 /* The same search over an explicit plan list with a caller objective (host
  * only; used to test the search strategies without a GPU).  `arch` and
- * `regs` (per-plan register counts, may be NULL = 32) feed the analytical
- * method.  Errors: INVALID_ARG. */
+ * `regs` (per-plan register counts, may be NULL = 32) and `smem` feed the
+ * analytical methods; MODEL takes the problem size from plans[0].n, a batch
+ * of 2^24 / n problems and the preset GB300 clock (2.07 GHz) and HBM rate
+ * (8.18 TB/s nominal).  Errors: INVALID_ARG. */
 int bplg_tune_plans_cost(const bplg_plan *plans, int32_t count, const int32_t *regs,
                          const int32_t *smem, const bplg_arch *arch, int32_t method, int32_t budget,
                          uint64_t seed, bplg_cost_fn cost, void *user, int32_t *chosen,
@@ -420,7 +440,7 @@ int bplg_tune_plans_cost(const bplg_plan *plans, int32_t count, const int32_t *r
 
 /* The plan for (op, dtype, n, batch) without any GPU evaluation ("online"
  * tuning, Section IV): the plan cached by an earlier bplg_tune_plan, else the
- * analytical guideline on the current device.
+ * plan of the GB300 cost model (BPLG_TUNE_MODEL) on the current device.
  * Errors: INVALID_ARG, UNSUPPORTED_SIZE, CUDA, NO_DEVICE. */
 int bplg_query_plan(int32_t op, int32_t dtype, int64_t n, int64_t batch, bplg_plan *out);
 

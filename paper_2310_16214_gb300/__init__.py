@@ -29,7 +29,7 @@ ERR_NO_DEVICE = -7
 I32, F32 = 0, 1
 OP_SCAN, OP_FFT, OP_TRIDIAG, OP_TRIDIAG_REFINED, OP_FFT_TC, OP_TRIDIAG_WM = 0, 1, 2, 3, 4, 5
 PATTERN_KS, PATTERN_LF = 0, 1
-TUNE_ANALYTIC, TUNE_LEARNED, TUNE_EXHAUSTIVE = 0, 1, 2
+TUNE_ANALYTIC, TUNE_LEARNED, TUNE_EXHAUSTIVE, TUNE_MODEL = 0, 1, 2, 3
 TC_BF16, TC_F16 = 0, 1
 
 EXPORTED = [

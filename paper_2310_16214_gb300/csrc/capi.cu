@@ -23,7 +23,8 @@ int device_space(int op, int dtype, int64_t n, std::vector<bplg_plan> *plans, st
                  std::vector<int> *smem);
 int tune_search(const std::vector<bplg_plan> &plans, const std::vector<int> &regs, const std::vector<int> &smem,
                 const bplg_arch &arch, int method, int budget, uint64_t seed,
-                const std::function<double(const bplg_plan &)> &cost, int *chosen, bplg_tune_report *rep);
+                const std::function<double(const bplg_plan &)> &cost, int *chosen, bplg_tune_report *rep,
+                const std::vector<double> *model_times);
 int tune_on_device(int op, int dtype, int64_t n, int64_t batch, int method, int budget, uint64_t seed,
                    bplg_plan *out, bplg_tune_report *rep);
 double time_plan(const bplg_plan &p, int dtype, int64_t n, int64_t batch, int reps, void *in, void *out,
@@ -302,7 +303,7 @@ int bplg_tune_plan(int32_t op, int32_t dtype, int64_t n, int64_t batch, int32_t 
     if (!out) return set_error(BPLG_ERR_INVALID_ARG, "null output");
     if (max_log_for(op) < 0) return set_error(BPLG_ERR_INVALID_ARG, "unknown op");
     if (batch < 1) return set_error(BPLG_ERR_INVALID_ARG, "batch must be >= 1");
-    if (method < BPLG_TUNE_ANALYTIC || method > BPLG_TUNE_EXHAUSTIVE) return set_error(BPLG_ERR_INVALID_ARG, "unknown method");
+    if (method < BPLG_TUNE_ANALYTIC || method > BPLG_TUNE_MODEL) return set_error(BPLG_ERR_INVALID_ARG, "unknown method");
     if (!size_ok(op, n, op == BPLG_OP_SCAN ? 1 : (op == BPLG_OP_FFT_TC ? 512 : 2)))
         return set_error(BPLG_ERR_UNSUPPORTED_SIZE, "unsupported size");
     return tune_on_device(op, dtype, n, batch, method, budget, seed, out, report);
@@ -313,8 +314,10 @@ int bplg_tune_plans_cost(const bplg_plan *plans, int32_t count, const int32_t *r
                          void *user, int32_t *chosen, bplg_tune_report *report) {
     clear_error();
     if (!plans || count <= 0 || !chosen) return set_error(BPLG_ERR_INVALID_ARG, "bad argument");
-    if (method != BPLG_TUNE_ANALYTIC && !cost) return set_error(BPLG_ERR_INVALID_ARG, "a cost function is required");
-    if (method == BPLG_TUNE_ANALYTIC && !arch) return set_error(BPLG_ERR_INVALID_ARG, "the analytical method needs arch limits");
+    if (method < BPLG_TUNE_ANALYTIC || method > BPLG_TUNE_MODEL) return set_error(BPLG_ERR_INVALID_ARG, "unknown method");
+    const bool analytical = method == BPLG_TUNE_ANALYTIC || method == BPLG_TUNE_MODEL;
+    if (!analytical && !cost) return set_error(BPLG_ERR_INVALID_ARG, "a cost function is required");
+    if (analytical && !arch) return set_error(BPLG_ERR_INVALID_ARG, "the analytical methods need arch limits");
     std::vector<bplg_plan> pv(plans, plans + count);
     std::vector<int> rv, sv;
     if (regs) rv.assign(regs, regs + count);
@@ -324,9 +327,17 @@ int bplg_tune_plans_cost(const bplg_plan *plans, int32_t count, const int32_t *r
         a = *arch;
     else
         arch_preset_gb300(&a);
+    std::vector<double> mt;
+    if (method == BPLG_TUNE_MODEL) {
+        const DevModel dm = dev_model_from_arch(a, 0.0, 0.0);
+        const int64_t n = plans[0].n > 0 ? plans[0].n : 1;
+        const int64_t batch = std::max<int64_t>(1, (int64_t(1) << 24) / n);
+        for (int i = 0; i < count; ++i)
+            mt.push_back(model_plan_time(pv[i], n, batch, rv.empty() ? 32 : rv[i], sv.empty() ? 0 : sv[i], 0, 0, dm));
+    }
     int ch = -1;
     int rc = tune_search(pv, rv, sv, a, method, budget, seed,
-                         [&](const bplg_plan &p) { return cost ? cost(&p, user) : NAN; }, &ch, report);
+                         [&](const bplg_plan &p) { return cost ? cost(&p, user) : NAN; }, &ch, report, &mt);
     *chosen = ch;
     return rc;
 }

@@ -17,6 +17,7 @@
 //   narrow_f64(x)          double -> float rounded to nearest, ties to even,
 //                          with overflow to ±inf and gradual underflow
 //   narrow_f64_ftz(x)      the same, inputs below 2^-126 flushed to ±0
+//   narrow_f64_ftz_pow2(x, k)  x * 2^k narrowed as narrow_f64_ftz, |k| <= 300
 //
 // IEEE-754 binary32: 1 sign, 8 exponent (bias 127), 23 fraction bits;
 // binary64: 1 sign, 11 exponent (bias 1023), 52 fraction bits.  A normal
@@ -155,14 +156,19 @@ BPLG_FPC float narrow_f64(double x) {
     return f32_from_bits(sign | static_cast<uint32_t>(q + inc));
 }
 
-// double -> float, round to nearest even, with inputs below 2^-126 in
+// (x * 2^k) as a float, round to nearest even, with results below 2^-126 in
 // magnitude flushed to signed zero (the flush-to-zero convention of FP32
-// arithmetic).  Branch-free; used where the float only feeds an FP32 solve.
-BPLG_FPC float narrow_f64_ftz(double x) {
+// arithmetic), for |k| <= 300.  The scale is an offset of the exponent
+// field, so it is exact and costs nothing; an x that is zero or a float64
+// subnormal gives signed zero.  Branch-free; used where the float only feeds
+// an FP32 solve (a residual narrowed after it has been scaled so that its
+// largest entry lies in [1/2, 1)).
+BPLG_FPC float narrow_f64_ftz_pow2(double x, int k) {
     const uint32_t hi = hi_f64(x), lo = lo_f64(x);
     const uint32_t sign = hi & 0x80000000u;
     const uint32_t ah = hi & 0x7FFFFFFFu;
-    const int fe = static_cast<int>(ah >> 20) - 896;
+    const int e = static_cast<int>(ah >> 20);
+    const int fe = e == 0 || e == 0x7FF ? (e == 0 ? 0 : 255) : e - 896 + k;
     const uint32_t base = (static_cast<uint32_t>(fe) << 23) + (((ah & 0x000FFFFFu) << 3) | (lo >> 29));
     const uint32_t rest = lo & 0x1FFFFFFFu;
     const uint32_t inc = (rest > 0x10000000u || (rest == 0x10000000u && (base & 1u))) ? 1u : 0u;
@@ -172,5 +178,9 @@ BPLG_FPC float narrow_f64_ftz(double x) {
     r = fe >= 255 ? (sign | (nan ? 0x7FC00000u : 0x7F800000u)) : r;
     return f32_from_bits(r);
 }
+
+// double -> float, round to nearest even, with inputs below 2^-126 in
+// magnitude flushed to signed zero.
+BPLG_FPC float narrow_f64_ftz(double x) { return narrow_f64_ftz_pow2(x, 0); }
 
 }  // namespace fpc

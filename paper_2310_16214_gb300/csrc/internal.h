@@ -112,6 +112,17 @@ int bo_best(const BoSearch *b);  // best valid plan seen, -1 if none
 int bo_evaluations(const BoSearch *b);
 void bo_destroy(BoSearch *b);
 
+// ---- GB300 analytical cost model (tune.cu)
+struct DevModel {
+    bplg_arch arch;
+    double clk;  // sustained SM clock, Hz
+    double bw;   // sustained HBM bandwidth, bytes/s
+};
+DevModel dev_model_from_arch(const bplg_arch &a, double peak_clock_hz, double nominal_bw);
+int dev_model_query(int dev, DevModel *out);
+double model_plan_time(const bplg_plan &p, int64_t n, int64_t batch, int regs, int smem, int regs2, int smem2,
+                       const DevModel &dm);
+
 // ---- plan cache (per process) and defaults
 bool cache_lookup(int op, int dtype, int64_t n, int64_t batch, bplg_plan *out);
 void cache_store(int op, int dtype, int64_t n, int64_t batch, const bplg_plan &p);

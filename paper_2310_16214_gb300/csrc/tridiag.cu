@@ -623,6 +623,48 @@ __device__ __forceinline__ float system_max1(float v, float *red, int wps, int &
     return r;
 }
 
+// The same two reductions for unsigned integers (high words of float64
+// magnitudes, whose unsigned order is the order of the magnitudes).
+__device__ __forceinline__ unsigned system_max_u(unsigned v, unsigned *red, int wps) {
+    v = __reduce_max_sync(kFullMask, v);
+    const int warp = threadIdx.x >> 5;
+    if ((threadIdx.x & 31) == 0) red[warp] = v;
+    __syncthreads();
+    const int w0 = warp - (warp & (wps - 1));
+    unsigned r = red[w0];
+    for (int k = 1; k < wps; ++k) r = max(r, red[w0 + k]);
+    __syncthreads();
+    return r;
+}
+__device__ __forceinline__ unsigned system_max1_u(unsigned v, unsigned *red, int wps, int &ph) {
+    v = __reduce_max_sync(kFullMask, v);
+    unsigned *slot = red + (ph & 1) * 32;
+    ph ^= 1;
+    const int warp = threadIdx.x >> 5;
+    if ((threadIdx.x & 31) == 0) slot[warp] = v;
+    __syncthreads();
+    const int w0 = warp - (warp & (wps - 1));
+    unsigned r = slot[w0];
+    for (int k = 1; k < wps; ++k) r = max(r, slot[w0 + k]);
+    return r;
+}
+
+// Scale of a residual from the largest high word of its float64 entries
+// (sign cleared): the exponent ex with max|r| in [2^(ex-1), 2^ex), clamped to
+// [-120, 120] so that 2^ex and 2^-ex stay normal floats (0 for r = 0).
+__device__ __forceinline__ int residual_exponent(unsigned rmax_hi) {
+    const int ex = rmax_hi ? static_cast<int>(rmax_hi >> 20) - 1022 : 0;
+    return ex < -120 ? -120 : (ex > 120 ? 120 : ex);
+}
+
+// Varah stopping threshold as a float64 high word: max|r| <= thr holds when
+// the residual's largest high word plus one (an upper bound of max|r|) is at
+// most this word.  rhs is 0 (never stop) or a normal float; the factor keeps
+// the margin of the float32 tests.
+__device__ __forceinline__ unsigned varah_hi(float rhs) {
+    return fpc::hi_f64(fpc::widen_f32_normal(rhs * (1.0f - 1e-5f)));
+}
+
 // 2^e as float64 and float32, built from the exponent bits (exact).
 __device__ __forceinline__ double pow2_f64(int e) {
     return __longlong_as_double(static_cast<long long>(1023 + e) << 52);
@@ -652,6 +694,7 @@ __global__ void __launch_bounds__(1024)
                            int max_iter, float tolf) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ float red[32];
+    __shared__ unsigned redu[32];
     __shared__ int done_sys[32];
     const int n = 1 << logn;
     const int tps = 1 << log_tps;
@@ -734,15 +777,19 @@ __global__ void __launch_bounds__(1024)
     const float dmarg = dmin > 0.f ? dmin * (1.0f - 1e-5f) : 0.f;
     // right-hand sides of the stopping tests below: 0 (never stop) unless
     // comfortably above the float32 subnormal range
-    const float varah_rhs = stop_rhs(tolf * xmaxf * dmarg);
+    const unsigned varah_thr = varah_hi(stop_rhs(tolf * xmaxf * dmarg));
     const float corr_rhs = stop_rhs(tolf * xmaxf);
 
     int applied = 0;
     for (int k = 0;; ++k) {
         // residual r = d - A x in float64 from the stored float32 coefficients;
         // widening and narrowing are integer operations, so the FP64 pipe
-        // carries only the three fused multiply-adds per equation
-        float rmaxf = 0.f;
+        // carries only the three fused multiply-adds per equation.  The
+        // float64 residual waits in the working row (its two halves in place
+        // of c and d) until its largest entry is known; it is then scaled by
+        // 2^-ex (max|r 2^-ex| in [1/2, 1)) as it is narrowed, so no entry is
+        // lost to float32 underflow whatever the system's scale.
+        unsigned rmax_hi = 0;
         for (int i = t; i < n; i += tps) {
             const float4 q = o[i];
             const double xl = i > 0 ? xs[i - 1] : 0.0;
@@ -758,14 +805,14 @@ __global__ void __launch_bounds__(1024)
                 r = fma(-fpc::widen_f32(q.y), xs[i], r);
                 r = fma(-fpc::widen_f32(q.z), xr, r);
             }
-            const float rf = fpc::narrow_f64_ftz(r);
-            rmaxf = fmaxf(rmaxf, fabsf(rf));
-            w[widx(i)] = make_float4(q.x, q.y, q.z, rf);
+            const unsigned rh = fpc::hi_f64(r);
+            rmax_hi = max(rmax_hi, rh & 0x7FFFFFFFu);
+            w[widx(i)] = make_float4(q.x, q.y, __uint_as_float(rh), __uint_as_float(fpc::lo_f64(r)));
         }
-        rmaxf = system_max(rmaxf, red, wps);
+        rmax_hi = system_max_u(rmax_hi, redu, wps);
         // the residual already bounds the error: stop before solving when
         // max|r| / delta <= tol max|x|
-        if (t == 0 && rmaxf * (1.0f + 1e-5f) <= varah_rhs)
+        if (t == 0 && rmax_hi + 1u <= varah_thr)
             done_sys[s] = 1;
         __syncthreads();
         {
@@ -774,16 +821,17 @@ __global__ void __launch_bounds__(1024)
             __syncthreads();
             if (all_done || k == max_iter) break;
         }
-        // sigma = 2^-ex brings max|r sigma| into [1/2, 1); the exponent is
-        // clamped so both powers of two stay normal
-        int ex = 0;
-        if (rmaxf > 0.f) frexpf(rmaxf, &ex);
-        ex = ex < -120 ? -120 : (ex > 120 ? 120 : ex);
-        const float sigma = pow2_f32(-ex);
-        for (int i = t; i < n; i += tps) dcomp(w, widx(i)) *= sigma;
+        // the scaled residual 2^-ex r, narrowed, becomes the right-hand side
+        const int ex = residual_exponent(rmax_hi);
+        for (int i = t; i < n; i += tps) {
+            const float4 row = w[widx(i)];
+            const float rf = fpc::narrow_f64_ftz_pow2(
+                fpc::f64_from_halves(__float_as_uint(row.z), __float_as_uint(row.w)), -ex);
+            w[widx(i)] = make_float4(row.x, row.y, o[i].z, rf);
+        }
         __syncthreads();
         solve();
-        const bool was_done = done_sys[s] != 0 || rmaxf == 0.f;
+        const bool was_done = done_sys[s] != 0 || rmax_hi == 0u;
         float emaxf = 0.f;
         for (int i = t; i < n; i += tps) {
             const float ep = xsol(i);
@@ -924,8 +972,9 @@ __device__ __forceinline__ void refined_reg_body(const float *ga, const float *g
     const float dmarg = dmin > 0.f ? dmin * (1.0f - 1e-5f) : 0.f;
     // right-hand sides of the stopping tests below: 0 (never stop) unless
     // comfortably above the float32 subnormal range
-    const float varah_rhs = stop_rhs(tolf * xmaxf * dmarg);
+    const unsigned varah_thr = varah_hi(stop_rhs(tolf * xmaxf * dmarg));
     const float corr_rhs = stop_rhs(tolf * xmaxf);
+    unsigned *redu = reinterpret_cast<unsigned *>(red);  // shares red's two sets of warp slots (ph)
 
     int applied = 0;
     for (int k = 0;; ++k) {
@@ -937,8 +986,12 @@ __device__ __forceinline__ void refined_reg_body(const float *ga, const float *g
         const double xr_nb = t < tps - 1 ? xfirst[tid + 1] : 0.0;
         // residual r = d - A x in float64 from the stored float32 coefficients;
         // widening and narrowing are integer operations, so the FP64 pipe
-        // carries only the three fused multiply-adds per equation
-        float rmaxf = 0.f;
+        // carries only the three fused multiply-adds per equation.  The
+        // float64 residual waits in ld (high half) and la (low half) until
+        // its largest entry is known; it is then scaled by 2^-ex (max|r 2^-ex|
+        // in [1/2, 1)) as it is narrowed, so no entry is lost to float32
+        // underflow whatever the system's scale.
+        unsigned rmax_hi = 0;
         auto residual = [&](auto fast_tag) {
             constexpr bool FAST = decltype(fast_tag)::value;
             auto widen = [](float f) { return FAST ? fpc::widen_f32_normal(f) : fpc::widen_f32(f); };
@@ -952,7 +1005,6 @@ __device__ __forceinline__ void refined_reg_body(const float *ga, const float *g
                     r = fma(-cb[i], xs[i], r);
                     r = fma(-cc[i], xr, r);
                     const float4 q = ocoef[i * blockDim.x];
-                    la[i] = q.x;
                     lb[i] = q.y;
                     lc[i] = q.z;
                 } else if constexpr (CO == 2) {
@@ -960,51 +1012,55 @@ __device__ __forceinline__ void refined_reg_body(const float *ga, const float *g
                     r = fma(-widen(q.x), xl, widen(q.w));
                     r = fma(-widen(q.y), xs[i], r);
                     r = fma(-widen(q.z), xr, r);
-                    la[i] = q.x;
                     lb[i] = q.y;
                     lc[i] = q.z;
                 } else {
                     r = fma(-widen(oa[i]), xl, widen(od[i]));
                     r = fma(-widen(ob[i]), xs[i], r);
                     r = fma(-widen(oc[i]), xr, r);
-                    la[i] = oa[i];
                     lb[i] = ob[i];
                     lc[i] = oc[i];
                 }
-                const float rf = fpc::narrow_f64_ftz(r);
-                rmaxf = fmaxf(rmaxf, fabsf(rf));
-                ld[i] = rf;
+                const unsigned rh = fpc::hi_f64(r);
+                rmax_hi = max(rmax_hi, rh & 0x7FFFFFFFu);
+                ld[i] = __uint_as_float(rh);
+                la[i] = __uint_as_float(fpc::lo_f64(r));
             }
         };
         if (fast)
             residual(std::true_type{});
         else
             residual(std::false_type{});
-        rmaxf = system_max1(rmaxf, red, wps, ph);
+        rmax_hi = system_max1_u(rmax_hi, redu, wps, ph);
         if (single) {
             // one system per block: every thread holds the same maxima and
             // takes the same decision, no flags or barriers needed
-            if (rmaxf * (1.0f + 1e-5f) <= varah_rhs || k == max_iter) break;
+            if (rmax_hi + 1u <= varah_thr || k == max_iter) break;
         } else {
-            if (t == 0 && rmaxf * (1.0f + 1e-5f) <= varah_rhs) done_sys[s] = 1;
+            if (t == 0 && rmax_hi + 1u <= varah_thr) done_sys[s] = 1;
             __syncthreads();
             int all_done = 1;
             for (int q = 0; q < spb; ++q) all_done &= done_sys[q];
             __syncthreads();
             if (all_done || k == max_iter) break;
         }
-        int ex = 0;
-        if (rmaxf > 0.f) frexpf(rmaxf, &ex);
-        ex = ex < -120 ? -120 : (ex > 120 ? 120 : ex);
-        const float sigma = pow2_f32(-ex);
+        // the scaled residual 2^-ex r, narrowed, becomes the right-hand side
+        const int ex = residual_exponent(rmax_hi);
 #pragma unroll
-        for (int i = 0; i < P; ++i) ld[i] *= sigma;
+        for (int i = 0; i < P; ++i) {
+            ld[i] = fpc::narrow_f64_ftz_pow2(fpc::f64_from_halves(__float_as_uint(ld[i]), __float_as_uint(la[i])),
+                                             -ex);
+            if constexpr (CO == 0)
+                la[i] = oa[i];
+            else
+                la[i] = ocoef[i * blockDim.x].x;
+        }
         if constexpr (SOLVER == 1) {
             wm::wm_solve_inreg<P, 2, 1>(la, lb, lc, ld, log_tps, wbuf);
         } else {
             cr_register_solve<P, PAD, SHUFFLE>(la, lb, lc, ld, log_m, log_tps, t, rows, bnd);
         }
-        const bool was_done = (!single && done_sys[s] != 0) || rmaxf == 0.f;
+        const bool was_done = (!single && done_sys[s] != 0) || rmax_hi == 0u;
         float emaxf = 0.f;
 #pragma unroll
         for (int i = 0; i < P; ++i) {

@@ -211,24 +211,285 @@ static bplg_candidate to_candidate(const bplg_plan &p, int regs, int smem) {
     return c;
 }
 
+// model time of every plan of a device space (the two-kernel FFT's row
+// kernel resources looked up here)
+int model_times_on_device(int dev, const std::vector<bplg_plan> &plans, const std::vector<int> &regs,
+                          const std::vector<int> &smem, int64_t n, int64_t batch, std::vector<double> *out) {
+    DevModel dm;
+    int rc = dev_model_query(dev, &dm);
+    if (rc != BPLG_OK) return rc;
+    out->assign(plans.size(), INFINITY);
+    for (size_t i = 0; i < plans.size(); ++i) {
+        int r2 = 0, s2 = 0;
+        if (plans[i].op == BPLG_OP_FFT && n > (int64_t(1) << kFftMaxLog)) {
+            Launch l2;
+            if (!fft_large_launch_info(plans[i], n, 1, -1, 1, &l2)) continue;
+            cudaFuncAttributes fa;
+            rc = func_attrs(l2.func, &fa);
+            if (rc != BPLG_OK) return rc;
+            r2 = fa.numRegs;
+            s2 = l2.smem + static_cast<int>(fa.sharedSizeBytes);
+        }
+        (*out)[i] = model_plan_time(plans[i], n, batch, regs[i], smem[i], r2, s2, dm);
+    }
+    return BPLG_OK;
+}
+
+// The default plan of a plan-less call: the GB300 cost model's choice for a
+// batch of 2^24 / n problems (or one problem above that size).
 int analytic_plan(int op, int dtype, int64_t n, bplg_plan *out) {
-    bplg_arch a;
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return cuda_error(e, "cudaGetDevice");
-    int rc = arch_query(dev, &a);
-    if (rc != BPLG_OK) return rc;
     std::vector<bplg_plan> plans;
     std::vector<int> regs, smem;
-    rc = device_space(op, dtype, n, &plans, &regs, &smem);
+    int rc = device_space(op, dtype, n, &plans, &regs, &smem);
     if (rc != BPLG_OK) return rc;
     if (plans.empty()) return set_error(BPLG_ERR_UNSUPPORTED_SIZE, "no valid plan for this size");
-    std::vector<bplg_candidate> c;
-    for (size_t i = 0; i < plans.size(); ++i) c.push_back(to_candidate(plans[i], regs[i], smem[i]));
-    int k = guideline_select(a, c.data(), static_cast<int>(c.size()), op == BPLG_OP_FFT || op == BPLG_OP_TRIDIAG_WM);
+    const int64_t batch = std::max<int64_t>(1, (int64_t(1) << 24) / n);
+    std::vector<double> t;
+    rc = model_times_on_device(dev, plans, regs, smem, n, batch, &t);
+    if (rc != BPLG_OK) return rc;
+    int k = -1;
+    for (size_t i = 0; i < plans.size(); ++i)
+        if (std::isfinite(t[i]) && (k < 0 || t[i] < t[k])) k = static_cast<int>(i);
     if (k < 0) return set_error(BPLG_ERR_UNSUPPORTED_SIZE, "no plan can launch");
     *out = plans[k];
     return BPLG_OK;
+}
+
+// ------------------------------------------------ GB300 analytical cost model
+// A zero-evaluation estimate of a plan's time on the current device, built
+// from the premises of Section IV-A restated for this GPU: coalescing (the
+// 128-byte lines a warp-wide global access touches), occupancy (resident
+// blocks from the kernel's real register and shared-memory counts), the
+// latency that resident work must hide (Little's law: B_a blocks in flight,
+// each living one HBM round trip plus its own transfer and compute time),
+// the instruction issue rate, barriers per stage, the block launch rate,
+// and, for the refined solve, the FP64 pipe.  The terms combine as a soft
+// maximum (an L4 norm), so the bound that dominates decides and the others
+// break ties.  Per-op instruction counts per thread follow the kernels'
+// algorithms (radix-r butterflies and exchanges per Stockham stage, CR
+// levels in registers or shared memory, Wang-Mou merge stages, the two
+// residuals and two solves of one refinement).  The constants are properties
+// of the device class, fixed once:
+//   latency          0.75 us  loaded HBM round trip of a block's first loads
+//   cpi              6        clocks per dependent instruction of one warp
+//   barrier          40       clocks per block barrier, x (1 + warps / 16)
+//   block launch     80 ns    per block per SM (launch and retire)
+//   issue            4        warp instructions per clock per SM
+//   line             1        clock per 128-byte line of a warp-wide access
+//   FP64             2        fused multiply-adds per clock per SM
+//   clock, bandwidth 0.92 x the peak SM clock, 0.83 x the nominal HBM rate
+//                    (what sustained streaming reaches)
+// A pipelined plan (bulk-copy ring) hides half the latency.
+namespace {
+
+constexpr double kModelLatency = 0.75e-6;
+constexpr double kModelCpi = 6.0;
+constexpr double kModelBarrier = 40.0;
+constexpr double kModelBlockLaunch = 80e-9;
+constexpr double kModelIpc = 4.0;
+constexpr double kModelLine = 1.0;
+constexpr double kModelFp64PerClk = 2.0;
+constexpr double kModelNorm = 4.0;
+
+struct ModelOp {
+    double instr = 0;   // instructions per thread
+    double bars = 0;    // block barriers
+    double bpe = 0;     // algorithmic HBM bytes per element
+    double acc = 0;     // warp-wide global access instructions per thread
+    double lines = 1;   // 128-byte lines per such access
+    bool piped = false; // bulk-copy ring in front of the loads
+    double fp64 = 0;    // FP64 pipe operations per element
+};
+
+int lg2i(int64_t v) { return ilog2(v < 1 ? 1 : v); }
+
+// lines of one warp-wide access when consecutive threads are `stride` bytes
+// apart and each moves `bytes`
+double warp_lines(double stride, double bytes) {
+    if (stride <= bytes) return std::max(1.0, std::ceil(32.0 * bytes / 128.0));
+    return std::min(32.0, std::max(1.0, std::ceil(32.0 * stride / 128.0)));
+}
+
+// lines of a warp-wide access over 32 threads in groups of g contiguous
+// `bytes`-wide elements, the groups far apart
+double grouped_lines(int64_t g, double bytes) {
+    if (g >= 32) return std::max(1.0, std::ceil(32.0 * bytes / 128.0));
+    return static_cast<double>(32 / g) * std::max(1.0, std::ceil(g * bytes / 128.0));
+}
+
+ModelOp model_op(const bplg_plan &p, int64_t n) {
+    ModelOp m;
+    const int P = std::max(1, p.P);
+    const int64_t tps = std::max<int64_t>(1, n / P);
+    switch (p.op) {
+        case BPLG_OP_SCAN:
+            m.bpe = 8;
+            m.instr = P * 2.0 + 14 + (tps > 32 ? 12 : 0);
+            m.bars = tps > 32 ? 1 : 0;
+            m.acc = 2.0 * std::max(1, P / 4);
+            m.lines = warp_lines(P * 4.0, P >= 4 ? 16.0 : P * 4.0);
+            break;
+        case BPLG_OP_FFT:
+        case BPLG_OP_FFT_TC: {
+            m.bpe = 16;
+            const int r = p.radix, lr = lg2i(r), logn = lg2i(n);
+            const int K = (logn + lr - 1) / lr;
+            const bool spec = p.smem_pad == 1 && ((p.io == 0 && ((r == 16 && logn >= 5 && logn <= 14) ||
+                                                                  (r == 8 && logn >= 4 && logn <= 9))) ||
+                                                  (p.io == 2 && r == 16 && logn >= 10 && logn <= 14));
+            const double bf = r == 2 ? 2.0 : r == 4 ? 3.0 : r == 8 ? 4.5 : 5.5;  // butterfly, per element
+            double idx = spec ? 0.5 : 3.0;                                       // stage index arithmetic
+            double xch = 2.0 * (K - 1) * (p.smem_pad ? 1.0 : 2.0);               // exchanges (bank conflicts unpadded)
+            if (p.smem_layout == 1) xch *= 2;                                    // real and imaginary in turn
+            double stage = bf + 3.0 + idx;                                       // + twiddle
+            if (p.op == BPLG_OP_FFT_TC) stage += p.io == 0 ? 6.0 : 30.0;          // hi/lo split, MMA round trip
+            m.instr = r * (K * stage + xch) + 12;
+            m.bars = 2.0 * (K - 1) + (p.op == BPLG_OP_FFT_TC ? 2.0 * K : 0.0);
+            if (p.io == 1) {
+                m.instr += r * 4;
+                m.bars += 2;
+                m.acc = 2.0 * std::max(1, r / 2);
+                m.lines = 4;
+            } else if (p.io == 0) {
+                m.acc = 2.0 * r;
+                m.lines = std::max(2.0, grouped_lines(tps, 8.0));
+            } else {
+                m.acc = 2.0 * std::max(1, r / 2);
+                m.lines = 4;
+                m.piped = true;
+            }
+            break;
+        }
+        case BPLG_OP_TRIDIAG: {
+            m.bpe = 20;
+            const int64_t mm = std::max(1, p.cr_switch);
+            const int lay = p.smem_layout;
+            const int lvl = std::max(0, lg2i(n / mm) - (lay == 2 ? lg2i(P) : 0));
+            const double per_eq = 20.0 * (p.smem_pad ? 1.0 : 2.0);
+            const double eq_thread = (lay == 2 ? static_cast<double>(n) / P : static_cast<double>(n)) / tps;
+            const bool shuf = p.shuffle && mm <= 32;
+            m.instr = P * 10.0 + (lay == 2 ? lg2i(P) * P * 6.0 : 0.0) + lvl * per_eq * std::max(1.0, eq_thread) +
+                      lg2i(mm) * (shuf ? 14.0 : 36.0) + 12;
+            m.bars = 2.0 * lvl + (shuf ? 0.0 : 2.0 * lg2i(mm)) + 2;
+            m.acc = 5.0 * std::max(1, P / 4);
+            m.lines = warp_lines(P * 4.0, P >= 4 ? 16.0 : P * 4.0);
+            m.piped = p.io == 1;
+            break;
+        }
+        case BPLG_OP_TRIDIAG_WM: {
+            m.bpe = 20;
+            const int r = p.radix, lr = lg2i(r);
+            const int st = tps > 1 ? (lg2i(tps) + lr - 1) / lr : 0;
+            const double merge = r == 2 ? 45.0 : r == 4 ? 100.0 : 220.0;
+            int smst = 0;
+            for (int k = 0; k < st; ++k)
+                if (!(p.shuffle && (k + 1) * lr <= 5)) ++smst;
+            m.instr = P * 20.0 + st * merge + smst * 10.0 + 12;
+            m.bars = 2.0 * smst + ((p.shuffle && tps <= 32) ? 0.0 : 1.0);
+            m.acc = 5.0 * std::max(1, P / 4);
+            m.lines = warp_lines(P * 4.0, P >= 4 ? 16.0 : P * 4.0);
+            break;
+        }
+        case BPLG_OP_TRIDIAG_REFINED: {
+            m.bpe = 24;
+            const int lay = p.smem_layout;
+            const double solve = lay == 7 ? P * 20.0 + lg2i(tps) * 45.0
+                                          : P * 30.0 + 150.0 + (lay >= 4 ? 0.0 : static_cast<double>(n) / tps * 40.0);
+            m.instr = 2 * solve + P * 70.0 + 100;
+            m.bars = lay == 7 ? 16 : 60;
+            m.acc = 6.0 * std::max(1, P / 4);
+            m.lines = warp_lines(P * 4.0, P >= 4 ? 16.0 : P * 4.0);
+            m.fp64 = 7;  // two residuals of 3 FMA and one update per element (one correction)
+            break;
+        }
+        default:
+            break;
+    }
+    return m;
+}
+
+// Time of one kernel: `blocks` blocks of `threads` threads over elems
+// elements, with this kernel's registers and shared memory.
+double model_kernel(const ModelOp &m, const DevModel &dm, int64_t elems, int64_t blocks, int threads, int regs,
+                    int smem, int spb_elems) {
+    int w_sm = 0, b_a = 0;
+    occupancy(dm.arch, (threads + 31) / 32, regs, smem, &w_sm, &b_a);
+    if (b_a <= 0) return INFINITY;
+    const double sms = dm.arch.num_sms;
+    const double wpb = (threads + 31) / 32;
+    const double per_sm_blocks = static_cast<double>(blocks) / sms;
+    const double bw_sm = dm.bw / sms;
+    const double t_xfer = static_cast<double>(spb_elems) * m.bpe / bw_sm;
+    const double t_comp = std::max(wpb * m.instr / kModelIpc, m.instr * kModelCpi) / dm.clk +
+                          m.bars * kModelBarrier * (1.0 + wpb / 16.0) / dm.clk;
+    const double res = kModelLatency * (m.piped ? 0.5 : 1.0) + t_xfer + t_comp;
+    const double terms[6] = {
+        per_sm_blocks * res / b_a,                                        // latency, b_a blocks in flight
+        static_cast<double>(elems) * m.bpe / dm.bw,                       // HBM bandwidth
+        per_sm_blocks * wpb * m.instr / (kModelIpc * dm.clk),             // issue
+        per_sm_blocks * wpb * m.acc * m.lines * kModelLine / dm.clk,      // lines through the load/store unit
+        per_sm_blocks * kModelBlockLaunch,                                // block launches
+        static_cast<double>(elems) * m.fp64 / (sms * kModelFp64PerClk * dm.clk)};  // FP64 pipe
+    double s = 0.0;
+    for (double t : terms) s += std::pow(t, kModelNorm);
+    return std::pow(s, 1.0 / kModelNorm);
+}
+
+}  // namespace
+
+DevModel dev_model_from_arch(const bplg_arch &a, double peak_clock_hz, double nominal_bw) {
+    DevModel d;
+    d.arch = a;
+    d.clk = 0.92 * (peak_clock_hz > 0 ? peak_clock_hz : 2.07e9);
+    d.bw = 0.83 * (nominal_bw > 0 ? nominal_bw : 8.18e12);
+    return d;
+}
+
+int dev_model_query(int dev, DevModel *out) {
+    bplg_arch a;
+    int rc = arch_query(dev, &a);
+    if (rc != BPLG_OK) return rc;
+    int clk_khz = 0, mem_khz = 0, bus_bits = 0;
+    cudaDeviceGetAttribute(&clk_khz, cudaDevAttrClockRate, dev);
+    cudaDeviceGetAttribute(&mem_khz, cudaDevAttrMemoryClockRate, dev);
+    cudaDeviceGetAttribute(&bus_bits, cudaDevAttrGlobalMemoryBusWidth, dev);
+    const double bw = 2.0 * mem_khz * 1e3 * bus_bits / 8.0;  // double data rate
+    *out = dev_model_from_arch(a, clk_khz * 1e3, bw);
+    return BPLG_OK;
+}
+
+// Modelled time (seconds) of plan p for (n, batch).  regs/smem are the
+// kernel's resources; for the two-kernel FFT regs2/smem2 are those of the
+// row kernel (the column kernel's are regs/smem).
+double model_plan_time(const bplg_plan &p, int64_t n, int64_t batch, int regs, int smem, int regs2, int smem2,
+                       const DevModel &dm) {
+    if (p.op == BPLG_OP_FFT && n > (int64_t(1) << kFftMaxLog) && p.n1_log > 0) {
+        const int l1 = p.n1_log, l2 = lg2i(n) - p.n1_log;
+        const int64_t n1 = int64_t(1) << l1, n2 = int64_t(1) << l2;
+        auto pass = [&](int64_t len, int per_block, int64_t cnt, int rg, int sm, double lines) {
+            bplg_plan q = p;
+            q.radix = q.P = 16;
+            q.io = 0;
+            q.smem_pad = 1;
+            q.smem_layout = 0;
+            ModelOp m = model_op(q, len);
+            m.instr += 16 * 4.0;  // the large-transform twiddle or the transposed store
+            m.lines = lines;
+            const int threads = static_cast<int>(per_block * (len / 16));
+            return model_kernel(m, dm, n * batch, batch * cnt, threads, rg, sm, static_cast<int>(per_block * len));
+        };
+        const double c = pass(n1, p.spb, n2 / std::max(1, p.spb), regs, smem, grouped_lines(p.spb, 8.0));
+        const double r = pass(n2, p.row_spb, n1 / std::max(1, p.row_spb), regs2 > 0 ? regs2 : regs,
+                              smem2 > 0 ? smem2 : smem, grouped_lines(p.row_spb, 8.0));
+        return c + r;
+    }
+    const ModelOp m = model_op(p, n);
+    const int64_t spb = std::max(1, p.spb);
+    const int64_t blocks = (batch + spb - 1) / spb;
+    return model_kernel(m, dm, n * batch, blocks, p.L, regs, smem, static_cast<int>(spb * n));
 }
 
 // ------------------------------------------------- Bayesian optimisation
@@ -558,7 +819,7 @@ void bo_destroy(BoSearch *b) { delete b; }
 
 int tune_search(const std::vector<bplg_plan> &plans, const std::vector<int> &regs, const std::vector<int> &smem,
                 const bplg_arch &arch, int method, int budget, uint64_t seed, const CostFn &cost, int *chosen,
-                bplg_tune_report *rep) {
+                bplg_tune_report *rep, const std::vector<double> *model_times) {
     bplg_tune_report r;
     std::memset(&r, 0, sizeof(r));
     r.method = method;
@@ -598,6 +859,18 @@ int tune_search(const std::vector<bplg_plan> &plans, const std::vector<int> &reg
             c.push_back(to_candidate(plans[i], regs.empty() ? 32 : regs[i], smem.empty() ? 0 : smem[i]));
         const bool radix = plans[0].op == BPLG_OP_FFT || plans[0].op == BPLG_OP_FFT_TC;
         *chosen = guideline_select(arch, c.data(), N, radix);
+        if (*chosen < 0) {
+            if (rep) *rep = r;
+            return set_error(BPLG_ERR_UNSUPPORTED_SIZE, "no candidate can launch");
+        }
+    } else if (method == BPLG_TUNE_MODEL) {
+        if (!model_times || model_times->size() != plans.size()) {
+            if (rep) *rep = r;
+            return set_error(BPLG_ERR_INVALID_ARG, "the cost model needs the plans' resources");
+        }
+        for (int i = 0; i < N; ++i)
+            if (std::isfinite((*model_times)[i]) && (*chosen < 0 || (*model_times)[i] < (*model_times)[*chosen]))
+                *chosen = i;
         if (*chosen < 0) {
             if (rep) *rep = r;
             return set_error(BPLG_ERR_UNSUPPORTED_SIZE, "no candidate can launch");
@@ -786,14 +1059,19 @@ int tune_on_device(int op, int dtype, int64_t n, int64_t batch, int method, int 
     if (rc != BPLG_OK) return rc;
     if (plans.empty()) return set_error(BPLG_ERR_UNSUPPORTED_SIZE, "no valid plan for this size");
     TimingArena arena;
-    if (method != BPLG_TUNE_ANALYTIC) {
+    if (method == BPLG_TUNE_LEARNED || method == BPLG_TUNE_EXHAUSTIVE) {
         rc = arena.open(op, dtype, n, batch);
+        if (rc != BPLG_OK) return rc;
+    }
+    std::vector<double> mt;
+    if (method == BPLG_TUNE_MODEL) {
+        rc = model_times_on_device(dev, plans, regs, smem, n, batch, &mt);
         if (rc != BPLG_OK) return rc;
     }
     const int reps = 25;
     CostFn cost = [&](const bplg_plan &p) { return arena.time(p, reps); };
     int chosen = -1;
-    rc = tune_search(plans, regs, smem, a, method, budget, seed, cost, &chosen, rep);
+    rc = tune_search(plans, regs, smem, a, method, budget, seed, cost, &chosen, rep, &mt);
     if (rc != BPLG_OK) return rc;
     *out = plans[chosen];
     cache_store(op, dtype, n, batch, *out);

@@ -51,6 +51,22 @@ static void narrow_case(uint64_t v) {
     }
 }
 
+// scaled narrowing: (x * 2^k) rounded to float with flush to zero below
+// 2^-126, for doubles x that are zero or normal (x * 2^k computed exactly by
+// ldexp: the tested k keep it normal in float64)
+static void narrow_pow2_case(uint64_t v, int k) {
+    const double x = from64(v);
+    if (std::fpclassify(x) == FP_SUBNORMAL) return;
+    const double xs = std::ldexp(x, k);
+    const float ref = std::fabs(xs) < std::ldexp(1.0, -126) ? std::copysign(0.0f, static_cast<float>(xs))
+                                                             : static_cast<float>(xs);
+    const float got = fpc::narrow_f64_ftz_pow2(x, k);
+    if (std::isnan(ref) ? !std::isnan(got) : bits32(got) != bits32(ref)) {
+        if (fails++ < 10) std::printf("narrow_pow2 %016llx k=%d: got %08x want %08x\n", (unsigned long long)v, k,
+                                      bits32(got), bits32(ref));
+    }
+}
+
 int main() {
     long n_w = 0, n_n = 0;
     // widen: every 61st bit pattern, all subnormals near the ends, all specials
@@ -87,6 +103,20 @@ int main() {
                             std::ldexp(1.0, -149), std::ldexp(1.0, -150), std::ldexp(1.5, -150), std::ldexp(1.0, -151),
                             std::ldexp(1.0, -126), std::ldexp(0.99999999, -126), 5e-324, 1e-310};
     for (double x : edges) { narrow_case(bits64(x)); narrow_case(bits64(-x)); n_n += 2; }
+    // scaled narrowing: exponents around the float range, shifts up to +-300
+    for (int j = 0; j < 20000000; ++j, ++n_n) {
+        const uint64_t r = next();
+        const int k = static_cast<int>((r >> 40) % 601) - 300;
+        const uint64_t e = static_cast<uint64_t>(896 - 40 - k + static_cast<int>((r >> 52) % 340));
+        if (e < 1 || e > 2046) continue;
+        narrow_pow2_case((r & 0x800FFFFFFFFFFFFFull) | (e << 52), k);
+    }
+    for (int k = -300; k <= 300; ++k) {
+        for (double x : edges) { narrow_pow2_case(bits64(x), k); narrow_pow2_case(bits64(-x), k); }
+        narrow_pow2_case(bits64(std::ldexp(1.0, -126 - k)), k);
+        narrow_pow2_case(bits64(std::ldexp(0.75, -126 - k)), k);
+        n_n += 2 * 19 + 2;
+    }
     std::printf("%s widen=%ld narrow=%ld fails=%ld\n", fails ? "FAIL" : "OK", n_w, n_n, fails);
     return fails ? 1 : 0;
 }

@@ -264,3 +264,57 @@ def test_grid_above_the_launch_limit_is_rejected_before_any_device_call():
     assert P.bplg_fft_batched_noalloc(16, 16, 64, 1 << 31, -1, ctypes.byref(fft), None) == bp.ERR_UNSUPPORTED_SIZE
     tri = bp.make_plan(bp.OP_TRIDIAG, 64, P=2, spb=1, cr_switch=32, shuffle=1)
     assert P.bplg_tridiag_batched(16, 16, 16, 16, 16, 64, 1 << 33, ctypes.byref(tri), None) == bp.ERR_UNSUPPORTED_SIZE
+
+
+# ------------------------------------------------- GB300 cost model (MODEL)
+
+def _scan_space(n):
+    """Every (P, spb) scan plan of size n with a plausible register count
+    (grows with the elements each thread holds) and no shared memory."""
+    plans, regs = [], []
+    for P in (1, 2, 4, 8, 16, 32):
+        tps = n // P
+        if tps < 1 or tps > 1024:
+            continue
+        for L in (32, 64, 128, 256, 512, 1024):
+            if L < tps or L % tps:
+                continue
+            plans.append(bp.make_plan(bp.OP_SCAN, n, P=P, spb=L // tps))
+            regs.append(16 + P + (16 if P == 32 else 0))
+    return plans, regs
+
+
+def test_cost_model_evaluates_nothing_and_is_deterministic():
+    plans, regs = _scan_space(1024)
+    calls = []
+    a = bp.arch_preset(1)
+    c1, rep = bp.tune_plans_cost(plans, lambda p: calls.append(1) or 1.0, bp.TUNE_MODEL, regs=regs,
+                                 smem=[0] * len(plans), arch=a)
+    c2, _ = bp.tune_plans_cost(plans, None, bp.TUNE_MODEL, regs=regs, smem=[0] * len(plans), arch=a)
+    assert calls == [] and rep.evaluations == 0 and c1 == c2 and 0 <= c1 < len(plans)
+
+
+def test_cost_model_premises_on_a_scan_space():
+    """Coalescing and bytes in flight: one element per thread cannot keep
+    HBM busy, and a block of one warp per 32 elements pays the launch rate;
+    the model picks several elements per thread and blocks of more than one
+    warp."""
+    plans, regs = _scan_space(1024)
+    c, _ = bp.tune_plans_cost(plans, None, bp.TUNE_MODEL, regs=regs, smem=[0] * len(plans), arch=bp.arch_preset(1))
+    assert plans[c].P >= 4 and plans[c].L >= 64
+
+
+def test_cost_model_skips_plans_that_cannot_launch():
+    plans, regs = _scan_space(256)
+    regs = [300 if p.P >= 4 else r for p, r in zip(plans, regs)]  # above the 255-register limit
+    c, _ = bp.tune_plans_cost(plans, None, bp.TUNE_MODEL, regs=regs, smem=[0] * len(plans), arch=bp.arch_preset(1))
+    assert plans[c].P < 4
+
+
+def test_cost_model_prefers_padded_exchanges():
+    """Bank conflicts: of two FFT plans that differ only in the padding of
+    the shared-memory exchange, the padded one is modelled faster."""
+    base = dict(P=16, spb=1, radix=16, smem_layout=0, io=0)
+    plans = [bp.make_plan(bp.OP_FFT, 4096, smem_pad=0, **base), bp.make_plan(bp.OP_FFT, 4096, smem_pad=1, **base)]
+    c, _ = bp.tune_plans_cost(plans, None, bp.TUNE_MODEL, regs=[60, 60], smem=[32768, 34816], arch=bp.arch_preset(1))
+    assert c == 1
