@@ -623,6 +623,22 @@ __device__ __forceinline__ float system_max1(float v, float *red, int wps, int &
     return r;
 }
 
+// Maximum of non-negative floats (magnitudes) over each system, with one
+// barrier: their bit patterns order like the values, so each warp reduces
+// them with one unsigned max.
+__device__ __forceinline__ float system_max1_nonneg(float v, float *red, int wps, int &ph) {
+    const unsigned w = __reduce_max_sync(kFullMask, __float_as_uint(v));
+    float *slot = red + (ph & 1) * 32;
+    ph ^= 1;
+    const int warp = threadIdx.x >> 5;
+    if ((threadIdx.x & 31) == 0) slot[warp] = __uint_as_float(w);
+    __syncthreads();
+    const int w0 = warp - (warp & (wps - 1));
+    float r = slot[w0];
+    for (int k = 1; k < wps; ++k) r = fmaxf(r, slot[w0 + k]);
+    return r;
+}
+
 // The same two reductions for unsigned integers (high words of float64
 // magnitudes, whose unsigned order is the order of the magnitudes).
 __device__ __forceinline__ unsigned system_max_u(unsigned v, unsigned *red, int wps) {
@@ -872,10 +888,13 @@ __global__ void __launch_bounds__(1024)
 // shared-memory refinement.  With SOLVER = 1 (refined smem_layout 7, the
 // coefficients as in layout 6) the float32 solves are the Wang-Mou divide
 // and conquer (radix-2 merges, shuffles within a warp) instead of CR/PCR.
-template <int P, int CO, int PAD, int SHUFFLE, int SOLVER>
+template <int P, int CO, int PAD, int SHUFFLE, int SOLVER, int LTPS = 0>
 __device__ __forceinline__ void refined_reg_body(const float *ga, const float *gb, const float *gc, const float *gd,
-                                                 double *x, int32_t *iters, int logn, int log_m, int log_tps, int spb,
+                                                 double *x, int32_t *iters, int logn, int log_m, int log_tps_rt, int spb,
                                                  int64_t batch, int max_iter, float tolf) {
+    // LTPS > 0: log2(threads per system) fixed at compile time (the
+    // Wang-Mou merge stages then unroll with constant lanes and radices)
+    const int log_tps = LTPS > 0 ? LTPS : log_tps_rt;
     constexpr int LP = (P >= 16) ? 4 : (P >= 8) ? 3 : (P >= 4) ? 2 : 1;
     constexpr int PF = CO == 0 ? P : 1;  // float32 coefficient registers (layout 4)
     constexpr int PD = CO == 1 ? P : 1;  // float64 coefficient registers (layout 5)
@@ -926,11 +945,21 @@ __device__ __forceinline__ void refined_reg_body(const float *ga, const float *g
     float dmin = 3.0e38f;
     // every coefficient of the block zero or normal (the usual case): the
     // residuals widen them with the short form
-    bool normal = true;
+    // (on the magnitudes' bit patterns: the largest below infinity -- NaN and
+    // inf fail -- and the smallest nonzero one at least 2^-126; a zero's
+    // pattern minus one wraps to the largest and drops out of the minimum)
+    unsigned amax = 0u, amin_m1 = 0xFFFFFFFFu;
 #pragma unroll
-    for (int i = 0; i < P; ++i)
-        normal = normal && fpc::f32_zero_or_normal(la[i]) && fpc::f32_zero_or_normal(lb[i]) &&
-                 fpc::f32_zero_or_normal(lc[i]) && fpc::f32_zero_or_normal(ld[i]);
+    for (int i = 0; i < P; ++i) {
+        const float v[4] = {la[i], lb[i], lc[i], ld[i]};
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const unsigned m = __float_as_uint(v[k]) & 0x7FFFFFFFu;
+            amax = max(amax, m);
+            amin_m1 = min(amin_m1, m - 1u);
+        }
+    }
+    const bool normal = amax < 0x7F800000u && amin_m1 >= 0x007FFFFFu;
     const bool fast = __syncthreads_and(normal) != 0;
 #pragma unroll
     for (int i = 0; i < P; ++i) {
@@ -966,7 +995,7 @@ __device__ __forceinline__ void refined_reg_body(const float *ga, const float *g
         xmaxf = fmaxf(xmaxf, fabsf(ld[i]));
     }
     int ph = 0;
-    xmaxf = system_max1(xmaxf, red, wps, ph);
+    xmaxf = system_max1_nonneg(xmaxf, red, wps, ph);
     // diagonal-dominance margin (see the shared-memory refinement)
     dmin = -system_max1(-dmin, red, wps, ph);
     const float dmarg = dmin > 0.f ? dmin * (1.0f - 1e-5f) : 0.f;
@@ -1004,22 +1033,15 @@ __device__ __forceinline__ void refined_reg_body(const float *ga, const float *g
                     r = fma(-ca[i], xl, cd[i]);
                     r = fma(-cb[i], xs[i], r);
                     r = fma(-cc[i], xr, r);
-                    const float4 q = ocoef[i * blockDim.x];
-                    lb[i] = q.y;
-                    lc[i] = q.z;
                 } else if constexpr (CO == 2) {
                     const float4 q = ocoef[i * blockDim.x];
                     r = fma(-widen(q.x), xl, widen(q.w));
                     r = fma(-widen(q.y), xs[i], r);
                     r = fma(-widen(q.z), xr, r);
-                    lb[i] = q.y;
-                    lc[i] = q.z;
                 } else {
                     r = fma(-widen(oa[i]), xl, widen(od[i]));
                     r = fma(-widen(ob[i]), xs[i], r);
                     r = fma(-widen(oc[i]), xr, r);
-                    lb[i] = ob[i];
-                    lc[i] = oc[i];
                 }
                 const unsigned rh = fpc::hi_f64(r);
                 rmax_hi = max(rmax_hi, rh & 0x7FFFFFFFu);
@@ -1044,16 +1066,24 @@ __device__ __forceinline__ void refined_reg_body(const float *ga, const float *g
             __syncthreads();
             if (all_done || k == max_iter) break;
         }
-        // the scaled residual 2^-ex r, narrowed, becomes the right-hand side
+        // the scaled residual 2^-ex r, narrowed, becomes the right-hand side;
+        // the correction solve's coefficients are read again only now, so
+        // that just the residual's two halves stay live across the reduction
         const int ex = residual_exponent(rmax_hi);
 #pragma unroll
         for (int i = 0; i < P; ++i) {
             ld[i] = fpc::narrow_f64_ftz_pow2(fpc::f64_from_halves(__float_as_uint(ld[i]), __float_as_uint(la[i])),
                                              -ex);
-            if constexpr (CO == 0)
+            if constexpr (CO == 0) {
                 la[i] = oa[i];
-            else
-                la[i] = ocoef[i * blockDim.x].x;
+                lb[i] = ob[i];
+                lc[i] = oc[i];
+            } else {
+                const float4 q = ocoef[i * blockDim.x];
+                la[i] = q.x;
+                lb[i] = q.y;
+                lc[i] = q.z;
+            }
         }
         if constexpr (SOLVER == 1) {
             wm::wm_solve_inreg<P, 2, 1>(la, lb, lc, ld, log_tps, wbuf);
@@ -1067,7 +1097,7 @@ __device__ __forceinline__ void refined_reg_body(const float *ga, const float *g
             if (!was_done) xs[i] += fpc::widen_f32_pow2(ld[i], ex);
             emaxf = fmaxf(emaxf, fabsf(ld[i]));
         }
-        emaxf = system_max1(emaxf, red, wps, ph);
+        emaxf = system_max1_nonneg(emaxf, red, wps, ph);
         if (!was_done) ++applied;
         const bool small = was_done || emaxf * pow2_f32(ex) * (1.0f + 1e-5f) <= corr_rhs;
         if (single) {
@@ -1103,29 +1133,37 @@ __global__ void __launch_bounds__(MAXT)
 // P = 8 and blocks of up to 128 threads: 72 registers, 7 blocks per SM
 // (0.256 ms at n = 1024, against 0.287 ms uncapped, 0.266 ms at 80 registers
 // and 0.272 ms at 64; the P = 16 form capped at 96 registers spilled 432
-// bytes and ran slower).
-template <int P, int CO, int PAD, int SHUFFLE, int MAXT, int SOLVER, int MINB>
+// bytes and ran slower).  LTPS > 0 fixes log2(threads per system) at
+// compile time.
+template <int P, int CO, int PAD, int SHUFFLE, int MAXT, int SOLVER, int MINB, int LTPS = 0>
 __global__ void __launch_bounds__(MAXT, MINB)
     tridiag_refined_reg_kernel_mb(const float *ga, const float *gb, const float *gc, const float *gd, double *x,
                                   int32_t *iters, int logn, int log_m, int log_tps, int spb, int64_t batch,
                                   int max_iter, float tolf) {
-    refined_reg_body<P, CO, PAD, SHUFFLE, SOLVER>(ga, gb, gc, gd, x, iters, logn, log_m, log_tps, spb, batch,
-                                                  max_iter, tolf);
+    refined_reg_body<P, CO, PAD, SHUFFLE, SOLVER, LTPS>(ga, gb, gc, gd, x, iters, logn, log_m, log_tps, spb, batch,
+                                                        max_iter, tolf);
 }
 
 namespace {
 
 // refined: layout bit 0 = float64 coefficient cache, bit 1 = compacted solver
 template <int PAD, int SHUFFLE>
-const void *tri_func_ps(bool refined, int layout, int io, int P, int threads) {
+const void *tri_func_ps(bool refined, int layout, int io, int P, int threads, int log_tps) {
     if (refined && layout == 7) {  // Wang-Mou solves: unpadded, shuffle merges only
         if constexpr (PAD == 0 && SHUFFLE == 1) {
             switch (P) {
                 case 2: return reinterpret_cast<const void *>(&tridiag_refined_reg_kernel<2, 2, 0, 1, 1024, 1>);
                 case 4: return reinterpret_cast<const void *>(&tridiag_refined_reg_kernel<4, 2, 0, 1, 1024, 1>);
                 case 8:
-                    if (threads <= 128)  // 72 registers: 7 blocks per SM
+                    if (threads <= 128) {  // 72 registers: 7 blocks per SM
+                        switch (log_tps) {  // merge stages unrolled at compile time
+                            case 5: return reinterpret_cast<const void *>(&tridiag_refined_reg_kernel_mb<8, 2, 0, 1, 128, 1, 7, 5>);
+                            case 6: return reinterpret_cast<const void *>(&tridiag_refined_reg_kernel_mb<8, 2, 0, 1, 128, 1, 7, 6>);
+                            case 7: return reinterpret_cast<const void *>(&tridiag_refined_reg_kernel_mb<8, 2, 0, 1, 128, 1, 7, 7>);
+                            default: break;
+                        }
                         return reinterpret_cast<const void *>(&tridiag_refined_reg_kernel_mb<8, 2, 0, 1, 128, 1, 7>);
+                    }
                     return reinterpret_cast<const void *>(&tridiag_refined_reg_kernel<8, 2, 0, 1, 512, 1>);
                 case 16: return reinterpret_cast<const void *>(&tridiag_refined_reg_kernel<16, 2, 0, 1, 256, 1>);
                 default: return nullptr;
@@ -1179,15 +1217,16 @@ const void *tri_func_ps(bool refined, int layout, int io, int P, int threads) {
     return reinterpret_cast<const void *>(&tridiag_kernel<PAD, SHUFFLE>);
 }
 
-const void *tri_func(int pad, int shuffle, bool refined, int layout, int io, int P, int threads) {
+const void *tri_func(int pad, int shuffle, bool refined, int layout, int io, int P, int threads, int log_tps) {
     if (pad < 0 || pad > 1 || shuffle < 0 || shuffle > 1 || layout < 0 || layout > 7 || io < 0 || io > 1)
         return nullptr;
     if (!refined && layout == 1 && (pad != 1 || io != 0)) return nullptr;
     if (!refined && layout == 2 && io == 1 && P < 4) return nullptr;
     if (pad)
-        return shuffle ? tri_func_ps<1, 1>(refined, layout, io, P, threads)
-                       : tri_func_ps<1, 0>(refined, layout, io, P, threads);
-    return shuffle ? tri_func_ps<0, 1>(refined, layout, io, P, threads) : tri_func_ps<0, 0>(refined, layout, io, P, threads);
+        return shuffle ? tri_func_ps<1, 1>(refined, layout, io, P, threads, log_tps)
+                       : tri_func_ps<1, 0>(refined, layout, io, P, threads, log_tps);
+    return shuffle ? tri_func_ps<0, 1>(refined, layout, io, P, threads, log_tps)
+                   : tri_func_ps<0, 0>(refined, layout, io, P, threads, log_tps);
 }
 
 }  // namespace
@@ -1230,7 +1269,8 @@ bool tridiag_launch_info(const bplg_plan &p, int64_t n, int64_t batch, bool refi
     std::string why;
     bplg_plan q = p;
     if (!plan_structurally_valid(q, BPLG_F32, n, &why)) return false;
-    const void *f = tri_func(p.smem_pad, p.shuffle, refined, p.smem_layout, refined ? 0 : p.io, p.P, p.L);
+    const void *f = tri_func(p.smem_pad, p.shuffle, refined, p.smem_layout, refined ? 0 : p.io, p.P, p.L,
+                             ilog2(n / p.P));
     if (!f) return false;
     out->func = f;
     out->threads = p.L;

@@ -158,6 +158,7 @@ __device__ __forceinline__ void wm_solve_inreg(float (&a)[P], float (&b)[P], flo
     const int nthr = blockDim.x;
     int par = 0;
     constexpr int LR = R >= 8 ? 3 : (R >= 4 ? 2 : 1);
+#pragma unroll
     for (int log_s = 0; log_s < log_tps;) {
         const int lrs = log_tps - log_s >= LR ? LR : log_tps - log_s;  // log2 of this stage's radix
         const int rs = 1 << lrs;
