@@ -34,6 +34,7 @@ int time_plan_owned(const bplg_plan &p, int dtype, int64_t n, int64_t batch, int
 int fft_device_status(int *flag, bool reset);
 int tridiag_device_status(int *flag, bool reset);
 int fft_tc_device_status(int *flag, bool reset);
+int fft_tc_gemm_device_status(int *flag, bool reset);
 
 namespace {
 std::mutex g_default_mu;
@@ -388,14 +389,16 @@ int bplg_online_status(int32_t op, int32_t dtype, int64_t n, int64_t batch, int3
 int bplg_device_status(int32_t *flag, int32_t reset) {
     clear_error();
     if (!flag) return set_error(BPLG_ERR_INVALID_ARG, "null output");
-    int f1 = 0, f2 = 0, f3 = 0;
+    int f1 = 0, f2 = 0, f3 = 0, f4 = 0;
     int rc = fft_device_status(&f1, reset != 0);
     if (rc != BPLG_OK) return rc;
     rc = tridiag_device_status(&f2, reset != 0);
     if (rc != BPLG_OK) return rc;
     rc = fft_tc_device_status(&f3, reset != 0);
     if (rc != BPLG_OK) return rc;
-    *flag = f1 ? f1 : (f2 ? f2 : f3);
+    rc = fft_tc_gemm_device_status(&f4, reset != 0);
+    if (rc != BPLG_OK) return rc;
+    *flag = f1 ? f1 : (f2 ? f2 : (f3 ? f3 : f4));
     return BPLG_OK;
 }
 

@@ -25,6 +25,7 @@
 #include "device_util.cuh"
 #include "fft_common.cuh"
 #include "internal.h"
+#include "tc_split.cuh"
 #include "tcgen05.cuh"
 
 namespace bplg {
@@ -36,11 +37,7 @@ template <>
 struct Split<BPLG_TC_BF16> {
     // pack (x0, x1) -> hi pair and lo pair (lower 16 bits: x0)
     static __device__ __forceinline__ void pack(float x0, float x1, uint32_t &hi, uint32_t &lo) {
-        const __nv_bfloat162 h = __floats2bfloat162_rn(x0, x1);
-        const float2 hf = __bfloat1622float2(h);
-        const __nv_bfloat162 l = __floats2bfloat162_rn(x0 - hf.x, x1 - hf.y);
-        hi = *reinterpret_cast<const uint32_t *>(&h);
-        lo = *reinterpret_cast<const uint32_t *>(&l);
+        HiLo<BPLG_TC_BF16>::pack(x0, x1, hi, lo);
     }
     static __device__ __forceinline__ void mma(float (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
         asm volatile(
@@ -55,11 +52,7 @@ struct Split<BPLG_TC_BF16> {
 template <>
 struct Split<BPLG_TC_F16> {
     static __device__ __forceinline__ void pack(float x0, float x1, uint32_t &hi, uint32_t &lo) {
-        const __half2 h = __floats2half2_rn(x0, x1);
-        const float2 hf = __half22float2(h);
-        const __half2 l = __floats2half2_rn(x0 - hf.x, x1 - hf.y);
-        hi = *reinterpret_cast<const uint32_t *>(&h);
-        lo = *reinterpret_cast<const uint32_t *>(&l);
+        HiLo<BPLG_TC_F16>::pack(x0, x1, hi, lo);
     }
     static __device__ __forceinline__ void mma(float (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
         asm volatile(
@@ -524,15 +517,22 @@ const void *tc_func(int prec, int dir, int threads, int io, int logn) {
 
 }  // namespace
 
+// the two-GEMM-pass kernels (fft_tc_gemm.cu)
+const void *fft_tc_gemm_func(int prec, int dir, int logn);
+int fft_tc_gemm_smem(int logn);
+int fft_tc_gemm_launch(const void *func, const void *in, void *out, int64_t n, int64_t batch, cudaStream_t s);
+
 // io 1 (mma.sync): the padded exchange tile; io 0 (tcgen05): the B matrices
-// (hi and lo, 4 KB) and the padded exchange tile, which the A matrices reuse
+// (hi and lo, 4 KB) and the padded exchange tile, which the A matrices reuse;
+// io 2: the 64-point DFT matrix and the data operand, both in two planes
 int fft_tc_smem_bytes(int64_t n, int spb, int io) {
+    if (io == 2) return fft_tc_gemm_smem(ilog2(n));
     return (io == 0 ? 4096 : 0) + spb * sig_stride<0, 1>(static_cast<int>(n)) * 8;
 }
 
 bool fft_tc_launch_info(const bplg_plan &p, int64_t n, int64_t batch, int prec, int dir, Launch *out) {
     if (!plan_structurally_valid(p, BPLG_F32, n, nullptr)) return false;
-    const void *f = tc_func(prec, dir, p.L, p.io, ilog2(n));
+    const void *f = p.io == 2 ? fft_tc_gemm_func(prec, dir, ilog2(n)) : tc_func(prec, dir, p.L, p.io, ilog2(n));
     if (!f) return false;
     out->func = f;
     out->threads = p.L;
@@ -548,6 +548,7 @@ int fft_tc_launch(const bplg_plan &p, const void *in, void *out, int64_t n, int6
         return set_error(BPLG_ERR_INVALID_PLAN, "fft tc: plan has no kernel");
     int rc = check_grid(li.blocks, "fft tc");
     if (rc != BPLG_OK) return rc;
+    if (p.io == 2) return fft_tc_gemm_launch(li.func, in, out, n, batch, s);
     const void *tw = nullptr;
     rc = twiddles_for_current_device(&tw);
     if (rc != BPLG_OK) return rc;

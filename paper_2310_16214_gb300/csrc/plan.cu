@@ -114,10 +114,18 @@ bool plan_structurally_valid(const bplg_plan &p, int dtype, int64_t n, std::stri
                 return fail(why, "FFT: the split-exchange pipelined variant is radix 16, padded, 1024 <= n <= 16384");
             return true;
         case BPLG_OP_FFT_TC:
+            if (p.io == 2) {
+                if (p.radix != 16 || p.smem_pad != 1 || p.smem_layout != 0 ||
+                    !((n == 4096 && p.P == 16 && p.spb == 2) || (n == 16384 && p.P == 32 && p.spb == 1)))
+                    return fail(why, "tensor-core FFT, two 64-point GEMM passes (io 2): n = 4096 (P 16, spb 2) or "
+                                     "16384 (P 32, spb 1), 512 threads, radix 16, padded interleaved");
+                return true;
+            }
             if (p.radix != 16 || p.P != 16) return fail(why, "tensor-core FFT: radix and P are 16");
             if (n < 512) return fail(why, "tensor-core FFT: n >= 512 (a warp per 32 butterflies)");
-            if (p.smem_pad != 1 || p.smem_layout != 0 || p.io < 0 || p.io > 1)
-                return fail(why, "tensor-core FFT: padded interleaved layout; io 0 (tcgen05) or 1 (mma.sync)");
+            if (p.smem_pad != 1 || p.smem_layout != 0 || p.io < 0 || p.io > 2)
+                return fail(why, "tensor-core FFT: padded interleaved layout; io 0 (tcgen05), 1 (mma.sync) or 2 "
+                                 "(two GEMM passes)");
             if (p.io == 0 && (n < 1024 || n > 16384 || p.L % 128 != 0))
                 return fail(why, "tensor-core FFT with tcgen05: 1024 <= n <= 16384 and blocks of 128-thread tiles");
             return true;
@@ -204,10 +212,10 @@ void plan_finalize(bplg_plan *p, int dtype, int64_t n) {
             p->S = plan_smem_bytes(*p, dtype, n) > 0 ? static_cast<int32_t>(p->spb * n) : 0;
             break;
         case BPLG_OP_FFT_TC:
-            p->radix = p->P;
+            p->radix = 16;
             p->shuffle = p->pattern = p->cr_switch = p->smem_layout = 0;
             p->smem_pad = 1;
-            if (p->io != 0) p->io = 1;
+            if (p->io != 0 && p->io != 2) p->io = 1;
             p->S = static_cast<int32_t>(p->spb * n);
             break;
         case BPLG_OP_TRIDIAG:
@@ -261,12 +269,15 @@ std::vector<bplg_plan> enumerate_structural(int op, int dtype, int64_t n) {
                     }
                 }
             } else if (op == BPLG_OP_FFT_TC) {
-                if (P != 16) continue;
                 p.radix = 16;
-                for (int io = 0; io <= 1; ++io) {
-                    p.io = io;
-                    push(p);
+                if (P == 16) {
+                    for (int io = 0; io <= 1; ++io) {
+                        p.io = io;
+                        push(p);
+                    }
                 }
+                p.io = 2;  // the two-GEMM-pass kernel: valid for one (P, spb) per size
+                push(p);
             } else if (op == BPLG_OP_FFT) {
                 if (P < 2 || P > 16) continue;
                 p.radix = P;

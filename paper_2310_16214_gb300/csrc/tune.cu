@@ -335,6 +335,17 @@ ModelOp model_op(const bplg_plan &p, int64_t n) {
         case BPLG_OP_FFT:
         case BPLG_OP_FFT_TC: {
             m.bpe = 16;
+            if (p.op == BPLG_OP_FFT_TC && p.io == 2) {
+                // two 64-point GEMM passes: per element a split and a store of
+                // each operand, one twiddle, the tensor-memory reads; the next
+                // tile's loads in flight behind the products
+                m.instr = P * 24.0 + 40;
+                m.bars = 4;
+                m.acc = 2.0 * P;
+                m.lines = 2;
+                m.piped = true;
+                break;
+            }
             const int r = p.radix, lr = lg2i(r), logn = lg2i(n);
             const int K = (logn + lr - 1) / lr;
             const bool spec = p.smem_pad == 1 && ((p.io == 0 && ((r == 16 && logn >= 5 && logn <= 14) ||

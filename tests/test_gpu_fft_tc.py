@@ -79,3 +79,37 @@ def test_argument_errors(bp):
     with pytest.raises(bp.BplgError) as e:
         bp.fft_tc_batched(z, z, 1024, 1, precision=7)
     assert e.value.code == bp.ERR_INVALID_ARG
+
+
+def _gemm_plan(bp, n):
+    plans = [p for p in bp.enumerate_plans(bp.OP_FFT_TC, bp.F32, n) if p.io == 2]
+    assert len(plans) == 1, plans
+    return plans[0]
+
+
+@pytest.mark.parametrize("n,batch", [(4096, 613), (16384, 311)])
+@pytest.mark.parametrize("prec", [0, 1])
+def test_two_gemm_pass_kernel_over_many_tiles(bp, n, batch, prec):
+    """The two-GEMM-pass kernel (io 2) with more tiles than persistent blocks
+    and, at n = 4096, an odd batch (a last tile of one signal): sampled
+    signals against the oracle, both directions, and no device error."""
+    plan = _gemm_plan(bp, n)
+    assert plan.L == 512
+    z = si.fft_c64(batch, n, stream=620 + n)
+    rows = np.unique(np.concatenate([sample_rows(batch, k=24), [batch - 1]]))
+    for d in (-1, 1):
+        X = run(bp, z, d, prec, plan)
+        err = fft_rel_err(X[rows], oracle.fft(z[rows], d)).max()
+        assert err <= 1e-5 * math.log2(n), (d, prec, err)
+    assert bp.device_status() == 0
+
+
+@pytest.mark.parametrize("n", [4096, 16384])
+def test_two_gemm_pass_kernel_in_place(bp, n):
+    plan = _gemm_plan(bp, n)
+    batch = 9
+    z = si.fft_c64(batch, n, stream=640 + n)
+    buf = c64_to_dev(z)
+    bp.fft_tc_batched(buf, buf, n, batch, -1, precision=1, plan=plan)
+    torch.cuda.synchronize()
+    assert fft_rel_err(c64_from_dev(buf), oracle.fft(z, -1)).max() <= 1e-5 * math.log2(n)
