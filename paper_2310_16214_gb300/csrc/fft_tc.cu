@@ -535,7 +535,7 @@ bool fft_tc_launch_info(const bplg_plan &p, int64_t n, int64_t batch, int prec, 
     const void *f = p.io == 2 ? fft_tc_gemm_func(prec, dir, ilog2(n)) : tc_func(prec, dir, p.L, p.io, ilog2(n));
     if (!f) return false;
     out->func = f;
-    out->threads = p.L;
+    out->threads = p.io == 2 ? p.L + 32 : p.L;  // io 2: L workers plus the warp that issues the products
     out->smem = fft_tc_smem_bytes(n, p.spb, p.io);
     out->blocks = (batch + p.spb - 1) / p.spb;
     return true;

@@ -16,26 +16,30 @@
 // 2k (2k + 1) gives the real (imaginary) part of output k from the inputs'
 // real parts (K columns 0..63) and imaginary parts (64..127).  Operands are
 // split into 16-bit hi and lo parts (tc_split.cuh) and every product is
-// Fl Dh + Fh Dl + Fh Dh, accumulated in float32 in tensor memory:
-//   pass 1: D1 = F x B1, B1 = the data (N = 64 columns per sub-signal,
-//           K = [re n2 | im n2]); D1 row (k2, part), column (sub-signal, n1)
-//   pass 2: D2 = A2 x F^T, A2 = the twiddled pass-1 output (rows (sub-signal,
-//           k2), K = [re n1 | im n1]); D2 row (sub-signal, k2), column
-//           (k1, part)
-// One copy of F in shared memory (K-major, 16-byte core matrices without
-// swizzle) serves as A in pass 1 and as B in pass 2.  Between the passes
-// each thread reads one row of D1 from tensor memory, swaps halves with its
-// neighbour lane (rows 2k2 and 2k2 + 1 hold the real and imaginary parts),
-// applies the twiddles in float32 from the float64-generated table, splits
-// and writes its row of A2.  D2 rows are read back with real and imaginary
-// parts side by side, and a warp's lanes hold consecutive outputs, so the
-// results go to global memory in 256-byte runs.
+// Fl Dh + Fh Dl + Fh Dh, accumulated in float32 in tensor memory.  F sits in
+// tensor memory (the A operand, one row per lane); the data are the B
+// operand in shared memory (K-major, 16-byte core matrices without
+// swizzle), so the tensor cores read one operand from shared memory:
+//   pass 1: D1 = F B1^T, B1 row (sub-signal, n1), K = [re n2 | im n2];
+//           D1 row (k2, part), column (sub-signal, n1)
+//   pass 2: D2 = F A2^T, A2 row (sub-signal, k2) = the twiddled pass-1
+//           output, K = [re n1 | im n1]; D2 row (k1, part), column
+//           (sub-signal, k2)
+// Between the passes each thread reads one row of D1 from tensor memory,
+// swaps halves with its neighbour lane (rows 2k and 2k + 1 hold the real
+// and imaginary parts), applies the twiddles in float32 (from the
+// float64-generated table, kept in shared memory), splits and writes its row
+// of A2 into the same buffer.  After pass 2 the same swap leaves each thread
+// eight consecutive outputs, written with 16-byte stores.
 //
-// Blocks are persistent (one per SM, 512 threads, 128 or 192 KB of shared
-// memory) and load the next tile -- two 4096-point signals or one
-// 16384-point signal -- into registers while the tensor cores run the
-// current one.  Waits on the MMA barrier are bounded: on a timeout the block
-// records the device error word and stops.
+// Blocks are persistent (one per SM, 512 threads, 160 KB of shared memory,
+// 512 tensor-memory columns) and load the next tile -- two 4096-point
+// signals or one 16384-point signal -- into registers while the tensor cores
+// run the current one.  For 4096 points two tiles are in flight, with two
+// data buffers and two tensor-memory slots: tile i + 1 is prepared and its
+// pass 1 runs while tile i's pass 2 runs and is written out.  Waits on the
+// MMA barriers are bounded: on a timeout the block records the device error
+// word and stops.
 #include "device_util.cuh"
 #include "fft_common.cuh"
 #include "internal.h"
@@ -46,10 +50,10 @@ namespace bplg {
 
 namespace {
 
-constexpr int kGemmThreads = 512;
+constexpr int kGemmThreads = 512;                 // worker threads (16 warps)
+constexpr int kGemmBlock = kGemmThreads + 32;     // + one warp that issues the products
 constexpr int kGemmK = 128;                     // real K of a 64-point DFT
 constexpr uint32_t kGemmSbo = 2048;             // bytes between 8-row groups (K = 128)
-constexpr int kGemmPlane = 128 * kGemmK * 2;    // one 16-bit plane of F (32 KB)
 
 // byte offset of element (row, k) of a K-major operand with K = 128
 __host__ __device__ constexpr uint32_t gemm_off(int row, int k) {
@@ -69,11 +73,27 @@ __device__ __forceinline__ uint64_t gemm_desc(uint32_t addr) {
 
 template <int LOGN>
 struct GemmShape {
-    static constexpr int SIG = LOGN == 12 ? 2 : 1;     // signals per tile
-    static constexpr int COLS = LOGN == 12 ? 128 : 256;  // pass-1 columns = pass-2 rows
-    static constexpr int EPT = LOGN == 12 ? 16 : 32;     // complex values each thread loads
-    static constexpr int DATA = COLS * kGemmK * 2;       // one 16-bit plane of the data operand
+    static constexpr int SIG = LOGN == 12 ? 2 : 1;       // signals per tile
+    static constexpr int ROWS = LOGN == 12 ? 128 : 256;  // pass-1 columns = pass-2 rows of a tile
+    static constexpr int NBUF = LOGN == 12 ? 2 : 1;      // tiles in flight (data buffers, tensor-memory slots)
+    static constexpr int PLANE = ROWS * kGemmK * 2;      // one 16-bit plane of a tile's data operand
+    static constexpr int SLOT_COLS = ROWS;               // tensor-memory columns of one tile's D
 };
+
+// tensor memory: F at columns 0..127 (hi planes 0..63, lo 64..127, two
+// 16-bit K elements per column), then NBUF slots of D
+constexpr uint32_t kGemmTmemCols = 512;
+constexpr uint32_t kGemmFCols = 128;
+
+// shared memory: the twiddles W4096^(n1 k2) (64 rows of 65, the pad
+// keeping rows 8 apart on other banks) and NBUF data buffers of two planes
+// each (at a 1 KB boundary)
+constexpr int kTwStride = 65;
+constexpr int kTwBytes = (64 * kTwStride * 8 + 1023) / 1024 * 1024;
+template <int LOGN>
+constexpr int gemm_smem_bytes() {
+    return kTwBytes + GemmShape<LOGN>::NBUF * 2 * GemmShape<LOGN>::PLANE;
+}
 
 // eight values (one K chunk) split and stored to both planes
 template <int PREC>
@@ -104,130 +124,164 @@ __device__ __forceinline__ float2 root(const float2 *__restrict__ tw, int m, int
     return w;
 }
 
-// issue the products of one pass on the calling thread: D (+)= A B^T over
-// K = 128, 8 steps of K = 16, three split products each
-template <int PREC>
-__device__ __forceinline__ void gemm_pass(uint32_t d, uint32_t a_hi, uint32_t a_lo, uint32_t b_hi, uint32_t b_lo,
+// issue the products of one pass on the calling thread: D = F B^T over
+// K = 128 with F in tensor memory, 8 steps of K = 16 (8 tensor-memory
+// columns of F, 256 bytes of B per step), three split products each
+__device__ __forceinline__ void gemm_pass(uint32_t d, uint32_t f_tmem, uint64_t b_hi, uint64_t b_lo,
                                           uint32_t idesc) {
 #pragma unroll
     for (int ks = 0; ks < kGemmK / 16; ++ks) {
-        const uint32_t k = static_cast<uint32_t>(ks) * 256;  // two 128-byte core matrices per step
-        umma_f16(d, gemm_desc(a_lo + k), gemm_desc(b_hi + k), idesc, ks > 0 ? 1u : 0u);
-        umma_f16(d, gemm_desc(a_hi + k), gemm_desc(b_lo + k), idesc, 1u);
-        umma_f16(d, gemm_desc(a_hi + k), gemm_desc(b_hi + k), idesc, 1u);
+        const uint32_t a_hi = f_tmem + static_cast<uint32_t>(8 * ks), a_lo = a_hi + 64;
+        const uint64_t k = static_cast<uint64_t>(ks) * (256 >> 4);
+        umma_f16_ts(d, a_lo, b_hi + k, idesc, ks > 0 ? 1u : 0u);
+        umma_f16_ts(d, a_hi, b_lo + k, idesc, 1u);
+        umma_f16_ts(d, a_hi, b_hi + k, idesc, 1u);
     }
 }
 
-// all threads: wait for the commit of the MMAs issued before; false (every
-// thread) if the bounded wait ran out
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+// wait for the completion of phase `phase` of `bar` (bounded; one lane of
+// the warp polls), then flip it
 __device__ __forceinline__ bool gemm_wait(uint64_t *bar, uint32_t &phase) {
-    bool arrived = true;
-    if (threadIdx.x < 32) arrived = mbar_wait_bounded(bar, phase);
-    const bool ok = __syncthreads_and(arrived) != 0;
+    bool ok = true;
+    if ((threadIdx.x & 31) == 0) ok = mbar_wait_bounded(bar, phase);
+    ok = __shfl_sync(kFullMask, ok ? 1 : 0, 0) != 0;
     phase ^= 1u;
-    tc_fence_after();
     return ok;
 }
 
 template <int PREC, int DIR, int LOGN>
-__global__ void __launch_bounds__(kGemmThreads, 1)
+__global__ void __launch_bounds__(kGemmBlock, 1)
     fft_tc_gemm_kernel(const float2 *__restrict__ in, float2 *__restrict__ out, const float2 *__restrict__ tw,
                        int64_t batch) {
     using G = GemmShape<LOGN>;
     constexpr int N = 1 << LOGN;
     extern __shared__ __align__(1024) unsigned char smem[];
-    unsigned char *f_hi = smem;
-    unsigned char *f_lo = smem + kGemmPlane;
-    unsigned char *d_hi = smem + 2 * kGemmPlane;
-    unsigned char *d_lo = d_hi + G::DATA;
-    __shared__ __align__(8) uint64_t bar;
+    float2 *tws = reinterpret_cast<float2 *>(smem);  // [n1][k2], rows kTwStride apart
+    unsigned char *dbuf = smem + kTwBytes;           // buffer b: hi plane, lo plane
+    // ready[b]: the workers have filled buffer b (and are done reading slot
+    // b); done[b]: the products over buffer b have completed
+    __shared__ __align__(8) uint64_t ready[G::NBUF];
+    __shared__ __align__(8) uint64_t done[G::NBUF];
     __shared__ uint32_t tmem_slot;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int64_t ntiles = (batch + G::SIG - 1) / G::SIG;
+    const bool mma_warp = warp == kGemmThreads / 32;
 
     if (warp == 0) {
-        tmem_alloc(&tmem_slot, G::COLS);
+        tmem_alloc(&tmem_slot, kGemmTmemCols);
         tmem_relinquish();
     }
     if (tid == 0) {
-        mbar_init(&bar, 1);
+#pragma unroll
+        for (int b = 0; b < G::NBUF; ++b) {
+            mbar_init(&ready[b], kGemmThreads / 32);  // one arrival per worker warp
+            mbar_init(&done[b], 1);
+        }
         fence_mbar_init();
     }
-    // F: row r = 2k + part_out, K column c = 64 part_in + n; W = exp(DIR 2 pi i k n / 64)
-    for (int e = tid; e < 128 * 64; e += kGemmThreads) {
-        const int r = e >> 6, c = (e & 63) * 2;
-        float v[2];
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            const int k = r >> 1, po = r & 1, pi = (c + h) >> 6, n = (c + h) & 63;
-            const float2 w = root<DIR>(tw, 64, (k * n) & 63);
-            v[h] = po == 0 ? (pi == 0 ? w.x : -w.y) : (pi == 0 ? w.y : w.x);
-        }
-        uint32_t hi, lo;
-        HiLo<PREC>::pack(v[0], v[1], hi, lo);
-        *reinterpret_cast<uint32_t *>(f_hi + gemm_off(r, c)) = hi;
-        *reinterpret_cast<uint32_t *>(f_lo + gemm_off(r, c)) = lo;
-    }
-    fence_proxy_async();
+    for (int e = tid; e < 64 * 64; e += kGemmBlock) tws[(e >> 6) * kTwStride + (e & 63)] = root<DIR>(tw, 4096, (e >> 6) * (e & 63));
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = tmem_slot;
-    const uint32_t sf_hi = smem_u32(f_hi), sf_lo = smem_u32(f_lo);
-    const uint32_t sd_hi = smem_u32(d_hi), sd_lo = smem_u32(d_lo);
     const uint32_t tq = static_cast<uint32_t>(32 * (warp & 3)) << 16;  // this warp's tensor-memory lanes
-    uint32_t phase = 0;
+    // F into tensor memory: row r = 2k + part_out in lane r, K column c =
+    // 64 part_in + n (W = exp(DIR 2 pi i k n / 64)) in column c / 2 of the hi
+    // or the lo half; each worker warp writes 32 columns of its lane quarter
+    if (!mma_warp) {
+        const int r = 32 * (warp & 3) + lane;
+        const int col0 = 32 * (warp >> 2);  // of the 128 F columns
+        uint32_t w32[32];
+#pragma unroll
+        for (int j = 0; j < 32; ++j) {
+            const int col = col0 + j, c = 2 * (col & 63);
+            float f[2];
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int k = r >> 1, po = r & 1, pi = (c + h) >> 6, n = (c + h) & 63;
+                const float2 w = root<DIR>(tw, 64, (k * n) & 63);
+                f[h] = po == 0 ? (pi == 0 ? w.x : -w.y) : (pi == 0 ? w.y : w.x);
+            }
+            uint32_t hi, lo;
+            HiLo<PREC>::pack(f[0], f[1], hi, lo);
+            w32[j] = col < 64 ? hi : lo;
+        }
+        tmem_st32(tmem + tq + static_cast<uint32_t>(col0), w32);
+        tmem_wait_st();
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    uint32_t ph_ready[G::NBUF], ph_done[G::NBUF];
+#pragma unroll
+    for (int b = 0; b < G::NBUF; ++b) ph_ready[b] = ph_done[b] = 0u;
     bool ok = true;
 
-    // thread -> (sub-signal or quarter, n1, n2 range) of the load
-    const int n1 = tid & 63;
-    float2 v[G::EPT];
+    auto plane_hi = [&](int b) { return dbuf + b * 2 * G::PLANE; };
+    auto plane_lo = [&](int b) { return dbuf + b * 2 * G::PLANE + G::PLANE; };
+
+    // ---- loads: LOGN 12: signal u, n1 pair (2np, 2np+1), n2 = 8g .. 8g+7 as
+    // 16-byte loads; LOGN 14: n1, n2 = 8g .. 8g+7, all four quarters
+    constexpr int NV = LOGN == 12 ? 8 : 16;
+    float4 v[NV];
     auto load = [&](int64_t tile) {
         if constexpr (LOGN == 12) {
-            const int u = tid >> 8, q = (tid >> 6) & 3;
+            const int u = tid >> 8, g = (tid >> 5) & 7, np = tid & 31;
             const int64_t sig = tile * 2 + u;
-            const float2 *src = in + sig * N + n1 + 64 * 16 * q;
+            const float4 *src = reinterpret_cast<const float4 *>(in + sig * N + 2 * np + 64 * 8 * g);
 #pragma unroll
-            for (int i = 0; i < 16; ++i) v[i] = sig < batch ? __ldcs(src + 64 * i) : make_float2(0.f, 0.f);
+            for (int i = 0; i < 8; ++i) v[i] = sig < batch ? __ldcs(src + 32 * i) : make_float4(0.f, 0.f, 0.f, 0.f);
         } else {
-            const int g = tid >> 6;
+            const int g = tid >> 6, n1 = tid & 63;
             const float2 *src = in + tile * N + n1 + 64 * 8 * g;
 #pragma unroll
             for (int i = 0; i < 8; ++i)
 #pragma unroll
-                for (int q = 0; q < 4; ++q) v[4 * i + q] = __ldcs(src + 64 * i + 4096 * q);
+                for (int q = 0; q < 4; q += 2) {
+                    const float2 a = __ldcs(src + 64 * i + 4096 * q), b = __ldcs(src + 64 * i + 4096 * (q + 1));
+                    v[2 * i + q / 2] = make_float4(a.x, a.y, b.x, b.y);
+                }
         }
     };
 
-    int64_t tile = blockIdx.x;
-    if (tile < ntiles) load(tile);
-    for (; tile < ntiles && ok; tile += gridDim.x) {
-        // ---- pass-1 operand: column (sub-signal, n1), K = [re n2 | im n2]
+    // ---- pass-1 operand of the loaded tile: row (sub-signal, n1), K = [re n2 | im n2]
+    auto prep = [&](int b) {
+        unsigned char *hp = plane_hi(b), *lp = plane_lo(b);
         if constexpr (LOGN == 12) {
-            const int u = tid >> 8, q = (tid >> 6) & 3;
-            const int row = u * 64 + n1;
+            const int u = tid >> 8, g = (tid >> 5) & 7, np = tid & 31;
+            // the thread's rows 2np and 2np + 1, the odd one first in every
+            // other group of four lanes: a warp's stores then cover all eight
+            // 16-byte bank slots
+            const int first = (np >> 2) & 1;
 #pragma unroll
-            for (int cc = 0; cc < 2; ++cc) {
+            for (int h = 0; h < 2; ++h) {
+                const int odd = h ^ first;
+                const int row = u * 64 + 2 * np + odd;
                 float re[8], im[8];
 #pragma unroll
-                for (int t = 0; t < 8; ++t) {
-                    re[t] = v[8 * cc + t].x;
-                    im[t] = v[8 * cc + t].y;
+                for (int i = 0; i < 8; ++i) {
+                    re[i] = odd ? v[i].z : v[i].x;
+                    im[i] = odd ? v[i].w : v[i].y;
                 }
-                put_chunk<PREC>(d_hi, d_lo, gemm_off(row, 16 * q + 8 * cc), re);
-                put_chunk<PREC>(d_hi, d_lo, gemm_off(row, 64 + 16 * q + 8 * cc), im);
+                put_chunk<PREC>(hp, lp, gemm_off(row, 8 * g), re);
+                put_chunk<PREC>(hp, lp, gemm_off(row, 64 + 8 * g), im);
             }
         } else {
-            // radix-4 first stage, two n2 at a time (few live registers), each
-            // output pair stored as one 32-bit word per plane
-            const int g = tid >> 6;
+            // radix-4 first stage, two n2 at a time, each output pair one
+            // 32-bit word per plane
+            const int g = tid >> 6, n1 = tid & 63;
 #pragma unroll
             for (int i = 0; i < 8; i += 2) {
                 float2 y[4][2];
 #pragma unroll
                 for (int h = 0; h < 2; ++h) {
-                    const float2 a0 = v[4 * (i + h)], a1 = v[4 * (i + h) + 1];
-                    const float2 a2 = v[4 * (i + h) + 2], a3 = v[4 * (i + h) + 3];
+                    const float4 p01 = v[2 * (i + h)], p23 = v[2 * (i + h) + 1];
+                    const float2 a0 = make_float2(p01.x, p01.y), a1 = make_float2(p01.z, p01.w);
+                    const float2 a2 = make_float2(p23.x, p23.y), a3 = make_float2(p23.z, p23.w);
                     const float2 s02 = cadd(a0, a2), d02 = csub(a0, a2), s13 = cadd(a1, a3), d13 = csub(a1, a3);
                     // DIR i (a1 - a3)
                     const float2 jd = DIR < 0 ? make_float2(d13.y, -d13.x) : make_float2(-d13.y, d13.x);
@@ -243,119 +297,167 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
                     HiLo<PREC>::pack(y[m][0].x, y[m][1].x, hr, lr);
                     HiLo<PREC>::pack(y[m][0].y, y[m][1].y, hi, li);
                     const uint32_t ore = gemm_off(m * 64 + n1, 8 * g + i), oim = gemm_off(m * 64 + n1, 64 + 8 * g + i);
-                    *reinterpret_cast<uint32_t *>(d_hi + ore) = hr;
-                    *reinterpret_cast<uint32_t *>(d_lo + ore) = lr;
-                    *reinterpret_cast<uint32_t *>(d_hi + oim) = hi;
-                    *reinterpret_cast<uint32_t *>(d_lo + oim) = li;
+                    *reinterpret_cast<uint32_t *>(hp + ore) = hr;
+                    *reinterpret_cast<uint32_t *>(lp + ore) = lr;
+                    *reinterpret_cast<uint32_t *>(hp + oim) = hi;
+                    *reinterpret_cast<uint32_t *>(lp + oim) = li;
                 }
             }
         }
-        fence_proxy_async();
-        tc_fence_before();
-        __syncthreads();
-        if (tid == 0) {
-            tc_fence_after();
-            gemm_pass<PREC>(tmem, sf_hi, sf_lo, sd_hi, sd_lo, umma_idesc_f16(HiLo<PREC>::kFmt, 128, G::COLS));
-            umma_commit(&bar);
-        }
-        // the next tile's loads are in flight while the tensor cores work
-        if (tile + gridDim.x < ntiles) load(tile + gridDim.x);
-        if (!gemm_wait(&bar, phase)) {
-            ok = false;
-            break;
-        }
+    };
 
-        // ---- D1 row (k2, part), columns (sub-signal, n1) -> twiddled A2 rows
-        {
-            const int r = 32 * (warp & 3) + lane;  // D1 row of this thread
-            const int k2 = r >> 1, odd = r & 1;
-            constexpr int CPW = G::COLS / 4;  // columns per warp: each lane quarter is read by 4 warps
-            const int c0 = CPW * (warp >> 2);
-#pragma unroll
-            for (int h = 0; h < CPW / 16; ++h) {
-                const int cb = c0 + 16 * h;  // 16 columns of one sub-signal
-                uint32_t raw[16];
-                tmem_ld16(tmem + tq + static_cast<uint32_t>(cb), raw);
-                tmem_wait_ld();
-                const int u = cb >> 6;
-                const int nb = (cb & 63) + 8 * odd;  // this thread keeps n1 = nb .. nb + 7
-                float re[8], im[8];
-#pragma unroll
-                for (int t = 0; t < 8; ++t) {
-                    const uint32_t send = odd ? raw[t] : raw[8 + t];
-                    const float got = __uint_as_float(__shfl_xor_sync(kFullMask, send, 1));
-                    const float2 z = odd ? make_float2(got, __uint_as_float(raw[8 + t]))
-                                         : make_float2(__uint_as_float(raw[t]), got);
-                    const float2 zt = cmul(z, root<DIR>(tw, 4096, ((nb + t) * k2) & 4095));
-                    re[t] = zt.x;
-                    im[t] = zt.y;
-                }
-                int row;
-                if constexpr (LOGN == 12)
-                    row = u * 64 + k2;
-                else
-                    row = 128 * (k2 >> 5) + 4 * (k2 & 31) + u;
-                put_chunk<PREC>(d_hi, d_lo, gemm_off(row, nb), re);
-                put_chunk<PREC>(d_hi, d_lo, gemm_off(row, 64 + nb), im);
-            }
-        }
-        fence_proxy_async();
-        tc_fence_before();
-        __syncthreads();
-        if (tid == 0) {
-            tc_fence_after();
-#pragma unroll
-            for (int hh = 0; hh < G::COLS / 128; ++hh) {
-                const uint32_t a = static_cast<uint32_t>(hh) * 16 * kGemmSbo;  // rows 128 hh ..
-                gemm_pass<PREC>(tmem + static_cast<uint32_t>(128 * hh), sd_hi + a, sd_lo + a, sf_hi, sf_lo,
-                                umma_idesc_f16(HiLo<PREC>::kFmt, 128, 128));
-            }
-            umma_commit(&bar);
-        }
-        if (!gemm_wait(&bar, phase)) {
-            ok = false;
-            break;
-        }
+    // ---- one pass over buffer b into slot b: D = F x B^T, N = ROWS (pass 1
+    // with the data, pass 2 with the twiddled pass-1 output in the buffer)
+    auto issue = [&](int b, uint64_t bh, uint64_t bl) {
+        gemm_pass(tmem + kGemmFCols + static_cast<uint32_t>(b * G::SLOT_COLS), tmem, bh, bl,
+                  umma_idesc_f16(HiLo<PREC>::kFmt, 128, G::ROWS));
+        umma_commit(&done[b]);
+    };
 
-        // ---- D2 row (sub-signal, k2), columns (k1, part) -> X
-        {
-            const int r = 32 * (warp & 3) + lane;
-            constexpr int CPW = G::COLS / 4;
-            const int c0 = CPW * (warp >> 2);
+    // ---- D1 row (k2, part), columns (sub-signal, n1) -> twiddled A2 rows in buffer b
+    auto epi1 = [&](int b) {
+        unsigned char *hp = plane_hi(b), *lp = plane_lo(b);
+        const int r = 32 * (warp & 3) + lane;  // D1 row of this thread
+        const int k2 = r >> 1, odd = r & 1;
+        constexpr int CPW = G::ROWS / 4;  // columns per warp: each lane quarter is read by 4 warps
+        const int c0 = CPW * (warp >> 2);
 #pragma unroll
-            for (int h = 0; h < CPW / 16; ++h) {
-                const int cb = c0 + 16 * h;
-                uint32_t raw[16];
-                tmem_ld16(tmem + tq + static_cast<uint32_t>(cb), raw);
-                tmem_wait_ld();
-                const int hh = cb >> 7;
-                const int k1b = (cb & 127) >> 1;  // eight outputs k1 = k1b .. k1b + 7
-                if constexpr (LOGN == 12) {
-                    const int u = r >> 6, k2 = r & 63;
-                    const int64_t sig = tile * 2 + u;
-                    if (sig < batch) {
-                        float2 *dst = out + sig * N + k2 + 64 * k1b;
+        for (int h = 0; h < CPW / 16; ++h) {
+            const int cb = c0 + 16 * h;  // 16 columns of one sub-signal
+            uint32_t raw[16];
+            tmem_ld16(tmem + tq + kGemmFCols + static_cast<uint32_t>(b * G::SLOT_COLS + cb), raw);
+            tmem_wait_ld();
+            const int u = cb >> 6;
+            const int nb = (cb & 63) + 8 * odd;  // this thread keeps n1 = nb .. nb + 7
+            float re[8], im[8];
 #pragma unroll
-                        for (int t = 0; t < 8; ++t)
-                            __stcs(dst + 64 * t, make_float2(__uint_as_float(raw[2 * t]), __uint_as_float(raw[2 * t + 1])));
-                    }
-                } else {
-                    // X[4 (k2 + 64 k1) + u] with u = r & 3, k2 = 32 hh + r / 4: lanes consecutive
-                    float2 *dst = out + tile * N + 128 * hh + r + 256 * k1b;
+            for (int t = 0; t < 8; ++t) {
+                const uint32_t send = odd ? raw[t] : raw[8 + t];
+                const float got = __uint_as_float(__shfl_xor_sync(kFullMask, send, 1));
+                const float2 z = odd ? make_float2(got, __uint_as_float(raw[8 + t]))
+                                     : make_float2(__uint_as_float(raw[t]), got);
+                const float2 zt = cmul(z, tws[(nb + t) * kTwStride + k2]);
+                re[t] = zt.x;
+                im[t] = zt.y;
+            }
+            // pass-2 operand row: (sub-signal, k2), sub-signal fastest for
+            // 16384 points (whose outputs X[4 (k2 + 64 k1) + u] interleave)
+            const int row = LOGN == 12 ? u * 64 + k2 : 4 * k2 + u;
+            put_chunk<PREC>(hp, lp, gemm_off(row, nb), re);
+            put_chunk<PREC>(hp, lp, gemm_off(row, 64 + nb), im);
+        }
+    };
+
+    // ---- D2 row (k1, part), columns = pass-2 operand rows of slot b -> X of
+    // `tile`: after the swap with the neighbour lane each thread holds eight
+    // consecutive outputs
+    auto epi2 = [&](int b, int64_t tile) {
+        const int r = 32 * (warp & 3) + lane;
+        const int k1 = r >> 1, odd = r & 1;
+        constexpr int CPW = G::ROWS / 4;
+        const int c0 = CPW * (warp >> 2);
 #pragma unroll
-                    for (int t = 0; t < 8; ++t)
-                        __stcs(dst + 256 * t, make_float2(__uint_as_float(raw[2 * t]), __uint_as_float(raw[2 * t + 1])));
-                }
+        for (int h = 0; h < CPW / 16; ++h) {
+            const int cb = c0 + 16 * h;
+            uint32_t raw[16];
+            tmem_ld16(tmem + tq + kGemmFCols + static_cast<uint32_t>(b * G::SLOT_COLS + cb), raw);
+            tmem_wait_ld();
+            const int rho = cb + 8 * odd;  // pass-2 operand rows rho .. rho + 7
+            float2 z[8];
+#pragma unroll
+            for (int t = 0; t < 8; ++t) {
+                const uint32_t send = odd ? raw[t] : raw[8 + t];
+                const float got = __uint_as_float(__shfl_xor_sync(kFullMask, send, 1));
+                z[t] = odd ? make_float2(got, __uint_as_float(raw[8 + t])) : make_float2(__uint_as_float(raw[t]), got);
+            }
+            float4 *dst;
+            bool live = true;
+            if constexpr (LOGN == 12) {
+                const int64_t sig = tile * 2 + (rho >> 6);
+                live = sig < batch;
+                dst = reinterpret_cast<float4 *>(out + sig * N + 64 * k1 + (rho & 63));
+            } else {
+                dst = reinterpret_cast<float4 *>(out + tile * N + 256 * k1 + rho);
+            }
+            if (live) {
+#pragma unroll
+                for (int t = 0; t < 4; ++t)
+                    __stcs(dst + t, make_float4(z[2 * t].x, z[2 * t].y, z[2 * t + 1].x, z[2 * t + 1].y));
             }
         }
-        tc_fence_before();
-        __syncthreads();  // tensor memory and the data planes are free for the next tile
+    };
+
+    // ---- the pipeline.  The workers fill a buffer, arrive on its `ready`
+    // barrier (after a proxy fence and a tensor-memory fence), and wait on its
+    // `done` barrier; the product warp waits on `ready`, issues the pass and
+    // commits it to `done`.  With two buffers, tile i + 1 is prepared and its
+    // pass 1 runs while tile i's pass 2 runs and is written out.
+    const int64_t stride = gridDim.x;
+    if (mma_warp) {
+        for (int64_t i = 0, tile = blockIdx.x; tile < ntiles && ok; ++i, tile += stride) {
+            const int b = G::NBUF == 2 ? static_cast<int>(i & 1) : 0;
+            const uint64_t bh = gemm_desc(smem_u32(plane_hi(b))), bl = gemm_desc(smem_u32(plane_lo(b)));
+            for (int pass = 0; pass < 2 && ok; ++pass) {
+                ok = gemm_wait(&ready[b], ph_ready[b]);
+                if (ok && lane == 0) {
+                    tc_fence_after();
+                    issue(b, bh, bl);
+                }
+                __syncwarp();
+            }
+        }
+    } else {
+        auto publish = [&](int b) {  // buffer b filled / slot b read by this warp
+            fence_proxy_async();
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&ready[b]);
+        };
+        int64_t tile = blockIdx.x;
+        if (tile < ntiles) {
+            load(tile);
+            prep(0);
+            publish(0);
+            if (tile + stride < ntiles) load(tile + stride);
+        }
+        for (int64_t i = 0; tile < ntiles; ++i, tile += stride) {
+            const int cur = G::NBUF == 2 ? static_cast<int>(i & 1) : 0;
+            const bool more = tile + stride < ntiles;
+            if (!gemm_wait(&done[cur], ph_done[cur])) {  // pass 1 of this tile
+                ok = false;
+                break;
+            }
+            tc_fence_after();
+            epi1(cur);
+            publish(cur);
+            if (G::NBUF == 2 && more) {
+                prep(cur ^ 1);
+                publish(cur ^ 1);
+                if (tile + 2 * stride < ntiles) load(tile + 2 * stride);
+            }
+            if (!gemm_wait(&done[cur], ph_done[cur])) {  // pass 2 of this tile
+                ok = false;
+                break;
+            }
+            tc_fence_after();
+            epi2(cur, tile);
+            if (G::NBUF == 1 && more) {
+                prep(0);
+                publish(0);  // also releases the slot read by epi2
+                if (tile + 2 * stride < ntiles) load(tile + 2 * stride);
+            }
+        }
     }
 
     tc_fence_before();
     __syncthreads();
-    if (!ok && tid == 0) mbar_wait_bounded(&bar, phase);  // let a late commit land before freeing
-    if (warp == 0) tmem_dealloc(tmem, G::COLS);
+    // a product still in flight after a timeout lands before the tensor
+    // memory is freed (bounded)
+    if (!__syncthreads_and(ok) && tid == 0) {
+#pragma unroll
+        for (int b = 0; b < G::NBUF; ++b) mbar_wait_bounded(&done[b], ph_done[b]);
+    }
+    if (warp == 0) tmem_dealloc(tmem, kGemmTmemCols);
 }
 
 template <int PREC, int DIR>
@@ -373,10 +475,7 @@ const void *fft_tc_gemm_func(int prec, int dir, int logn) {
     return nullptr;
 }
 
-// F (two planes) and the data operand (two planes)
-int fft_tc_gemm_smem(int logn) {
-    return 2 * kGemmPlane + 2 * (logn == 12 ? GemmShape<12>::DATA : GemmShape<14>::DATA);
-}
+int fft_tc_gemm_smem(int logn) { return logn == 12 ? gemm_smem_bytes<12>() : gemm_smem_bytes<14>(); }
 
 // persistent launch: one block per SM at most, tiles of two 4096-point
 // signals or one 16384-point signal
@@ -390,12 +489,12 @@ int fft_tc_gemm_launch(const void *func, const void *in, void *out, int64_t n, i
     if (rc != BPLG_OK) return rc;
     const int64_t ntiles = logn == 12 ? (batch + 1) / 2 : batch;
     int64_t grid = 0;
-    rc = persistent_grid(func, kGemmThreads, smem, ntiles, &grid);
+    rc = persistent_grid(func, kGemmBlock, smem, ntiles, &grid);
     if (rc != BPLG_OK) return rc;
     void *args[] = {(void *)&in, (void *)&out, (void *)&tw, &batch};
-    cudaError_t e = cudaLaunchKernel(func, dim3(static_cast<unsigned>(grid)), dim3(kGemmThreads), args,
+    cudaError_t e = cudaLaunchKernel(func, dim3(static_cast<unsigned>(grid)), dim3(kGemmBlock), args,
                                      static_cast<size_t>(smem), s);
-    return e == cudaSuccess ? BPLG_OK : launch_error(e, "fft tc (two GEMM passes) launch", func, grid, kGemmThreads, smem);
+    return e == cudaSuccess ? BPLG_OK : launch_error(e, "fft tc (two GEMM passes) launch", func, grid, kGemmBlock, smem);
 }
 
 // Read (and optionally clear) the device error word of this file's kernel
