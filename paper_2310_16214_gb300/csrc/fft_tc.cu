@@ -520,6 +520,7 @@ const void *tc_func(int prec, int dir, int threads, int io, int logn) {
 // the two-GEMM-pass kernels (fft_tc_gemm.cu)
 const void *fft_tc_gemm_func(int prec, int dir, int logn);
 int fft_tc_gemm_smem(int logn);
+int fft_tc_gemm_threads(int logn);
 int fft_tc_gemm_launch(const void *func, const void *in, void *out, int64_t n, int64_t batch, cudaStream_t s);
 
 // io 1 (mma.sync): the padded exchange tile; io 0 (tcgen05): the B matrices
@@ -535,7 +536,7 @@ bool fft_tc_launch_info(const bplg_plan &p, int64_t n, int64_t batch, int prec, 
     const void *f = p.io == 2 ? fft_tc_gemm_func(prec, dir, ilog2(n)) : tc_func(prec, dir, p.L, p.io, ilog2(n));
     if (!f) return false;
     out->func = f;
-    out->threads = p.io == 2 ? p.L + 32 : p.L;  // io 2: L workers plus the warp that issues the products
+    out->threads = p.io == 2 ? fft_tc_gemm_threads(ilog2(n)) : p.L;
     out->smem = fft_tc_smem_bytes(n, p.spb, p.io);
     out->blocks = (batch + p.spb - 1) / p.spb;
     return true;

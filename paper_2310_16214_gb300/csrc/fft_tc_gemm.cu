@@ -50,8 +50,7 @@ namespace bplg {
 
 namespace {
 
-constexpr int kGemmThreads = 512;                 // worker threads (16 warps)
-constexpr int kGemmBlock = kGemmThreads + 32;     // + one warp that issues the products
+constexpr int kGemmThreads = 512;  // worker threads (16 warps)
 constexpr int kGemmK = 128;                     // real K of a 64-point DFT
 constexpr uint32_t kGemmSbo = 2048;             // bytes between 8-row groups (K = 128)
 
@@ -78,6 +77,11 @@ struct GemmShape {
     static constexpr int NBUF = LOGN == 12 ? 2 : 1;      // tiles in flight (data buffers, tensor-memory slots)
     static constexpr int PLANE = ROWS * kGemmK * 2;      // one 16-bit plane of a tile's data operand
     static constexpr int SLOT_COLS = ROWS;               // tensor-memory columns of one tile's D
+    // 4096 points: a 17th warp issues the products (96 registers a thread);
+    // 16384 points: one lane of warp 0 does, leaving 128 registers a thread
+    // for the prefetched tile
+    static constexpr bool ISSUER_WARP = LOGN == 12;
+    static constexpr int BLOCK = kGemmThreads + (ISSUER_WARP ? 32 : 0);
 };
 
 // tensor memory: F at columns 0..127 (hi planes 0..63, lo 64..127, two
@@ -90,9 +94,12 @@ constexpr uint32_t kGemmFCols = 128;
 // each (at a 1 KB boundary)
 constexpr int kTwStride = 65;
 constexpr int kTwBytes = (64 * kTwStride * 8 + 1023) / 1024 * 1024;
+// 16384 points: the radix-4 stage's twiddle W16384^(m k), k = n1 + 64 n2,
+// as the product W16384^(m n1) W256^(m n2) of two 3 x 64 tables
+constexpr int kTw14Bytes = 2 * 3 * 64 * 8;
 template <int LOGN>
 constexpr int gemm_smem_bytes() {
-    return kTwBytes + GemmShape<LOGN>::NBUF * 2 * GemmShape<LOGN>::PLANE;
+    return kTwBytes + GemmShape<LOGN>::NBUF * 2 * GemmShape<LOGN>::PLANE + (LOGN == 14 ? kTw14Bytes : 0);
 }
 
 // eight values (one K chunk) split and stored to both planes
@@ -139,22 +146,30 @@ __device__ __forceinline__ void gemm_pass(uint32_t d, uint32_t f_tmem, uint64_t 
     }
 }
 
+// barrier of the worker warps alone (named barrier 1)
+__device__ __forceinline__ void workers_sync() {
+    asm volatile("bar.sync 1, %0;" ::"n"(kGemmThreads) : "memory");
+}
+
 __device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
 
 // wait for the completion of phase `phase` of `bar` (bounded; one lane of
-// the warp polls), then flip it
-__device__ __forceinline__ bool gemm_wait(uint64_t *bar, uint32_t &phase) {
-    bool ok = true;
-    if ((threadIdx.x & 31) == 0) ok = mbar_wait_bounded(bar, phase);
-    ok = __shfl_sync(kFullMask, ok ? 1 : 0, 0) != 0;
+// the warp polls), then flip it.  After a timeout (ok false) nothing is
+// waited for any more: the warp runs on through the same barriers as the
+// others and the block ends with the device error word set.
+__device__ __forceinline__ void gemm_wait(uint64_t *bar, uint32_t &phase, bool &ok) {
+    if (ok) {
+        bool got = true;
+        if ((threadIdx.x & 31) == 0) got = mbar_wait_bounded(bar, phase);
+        ok = __shfl_sync(kFullMask, got ? 1 : 0, 0) != 0;
+    }
     phase ^= 1u;
-    return ok;
 }
 
 template <int PREC, int DIR, int LOGN>
-__global__ void __launch_bounds__(kGemmBlock, 1)
+__global__ void __launch_bounds__(GemmShape<LOGN>::BLOCK, 1)
     fft_tc_gemm_kernel(const float2 *__restrict__ in, float2 *__restrict__ out, const float2 *__restrict__ tw,
                        int64_t batch) {
     using G = GemmShape<LOGN>;
@@ -162,6 +177,8 @@ __global__ void __launch_bounds__(kGemmBlock, 1)
     extern __shared__ __align__(1024) unsigned char smem[];
     float2 *tws = reinterpret_cast<float2 *>(smem);  // [n1][k2], rows kTwStride apart
     unsigned char *dbuf = smem + kTwBytes;           // buffer b: hi plane, lo plane
+    // 16384 points: W16384^(m n1) at [m - 1][n1], W256^(m n2) at [3 + m - 1][n2]
+    float2 *tw14 = reinterpret_cast<float2 *>(dbuf + G::NBUF * 2 * G::PLANE);
     // ready[b]: the workers have filled buffer b (and are done reading slot
     // b); done[b]: the products over buffer b have completed
     __shared__ __align__(8) uint64_t ready[G::NBUF];
@@ -169,7 +186,6 @@ __global__ void __launch_bounds__(kGemmBlock, 1)
     __shared__ uint32_t tmem_slot;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int64_t ntiles = (batch + G::SIG - 1) / G::SIG;
-    const bool mma_warp = warp == kGemmThreads / 32;
 
     if (warp == 0) {
         tmem_alloc(&tmem_slot, kGemmTmemCols);
@@ -183,7 +199,15 @@ __global__ void __launch_bounds__(kGemmBlock, 1)
         }
         fence_mbar_init();
     }
-    for (int e = tid; e < 64 * 64; e += kGemmBlock) tws[(e >> 6) * kTwStride + (e & 63)] = root<DIR>(tw, 4096, (e >> 6) * (e & 63));
+    for (int e = tid; e < 64 * 64; e += G::BLOCK)
+        tws[(e >> 6) * kTwStride + (e & 63)] = root<DIR>(tw, 4096, (e >> 6) * (e & 63));
+    if constexpr (LOGN == 14) {
+        for (int e = tid; e < 3 * 64; e += G::BLOCK) {
+            const int m = e / 64 + 1, j = e % 64;
+            tw14[e] = root<DIR>(tw, 16384, m * j);
+            tw14[3 * 64 + e] = root<DIR>(tw, 256, m * j);
+        }
+    }
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
@@ -192,7 +216,7 @@ __global__ void __launch_bounds__(kGemmBlock, 1)
     // F into tensor memory: row r = 2k + part_out in lane r, K column c =
     // 64 part_in + n (W = exp(DIR 2 pi i k n / 64)) in column c / 2 of the hi
     // or the lo half; each worker warp writes 32 columns of its lane quarter
-    if (!mma_warp) {
+    if (warp < kGemmThreads / 32) {
         const int r = 32 * (warp & 3) + lane;
         const int col0 = 32 * (warp >> 2);  // of the 128 F columns
         uint32_t w32[32];
@@ -271,37 +295,39 @@ __global__ void __launch_bounds__(kGemmBlock, 1)
                 put_chunk<PREC>(hp, lp, gemm_off(row, 64 + 8 * g), im);
             }
         } else {
-            // radix-4 first stage, two n2 at a time, each output pair one
-            // 32-bit word per plane
+            // radix-4 first stage in place (v[2i] <- y0, y1 and v[2i + 1] <-
+            // y2, y3 of n2 = 8g + i); then for each output quarter m the
+            // thread's eight consecutive n2 form one 16-byte chunk per plane
+            // and part
             const int g = tid >> 6, n1 = tid & 63;
+            const float2 w1 = tw14[n1], w2 = tw14[64 + n1], w3 = tw14[128 + n1];  // W16384^(m n1)
 #pragma unroll
-            for (int i = 0; i < 8; i += 2) {
-                float2 y[4][2];
+            for (int i = 0; i < 8; ++i) {
+                const float4 p01 = v[2 * i], p23 = v[2 * i + 1];
+                const float2 a0 = make_float2(p01.x, p01.y), a1 = make_float2(p01.z, p01.w);
+                const float2 a2 = make_float2(p23.x, p23.y), a3 = make_float2(p23.z, p23.w);
+                const float2 s02 = cadd(a0, a2), d02 = csub(a0, a2), s13 = cadd(a1, a3), d13 = csub(a1, a3);
+                // DIR i (a1 - a3)
+                const float2 jd = DIR < 0 ? make_float2(d13.y, -d13.x) : make_float2(-d13.y, d13.x);
+                const int n2 = 8 * g + i;  // W256^(m n2)
+                const float2 y0 = cadd(s02, s13);
+                const float2 y1 = cmul(cadd(d02, jd), cmul(w1, tw14[3 * 64 + n2]));
+                const float2 y2 = cmul(csub(s02, s13), cmul(w2, tw14[4 * 64 + n2]));
+                const float2 y3 = cmul(csub(d02, jd), cmul(w3, tw14[5 * 64 + n2]));
+                v[2 * i] = make_float4(y0.x, y0.y, y1.x, y1.y);
+                v[2 * i + 1] = make_float4(y2.x, y2.y, y3.x, y3.y);
+            }
 #pragma unroll
-                for (int h = 0; h < 2; ++h) {
-                    const float4 p01 = v[2 * (i + h)], p23 = v[2 * (i + h) + 1];
-                    const float2 a0 = make_float2(p01.x, p01.y), a1 = make_float2(p01.z, p01.w);
-                    const float2 a2 = make_float2(p23.x, p23.y), a3 = make_float2(p23.z, p23.w);
-                    const float2 s02 = cadd(a0, a2), d02 = csub(a0, a2), s13 = cadd(a1, a3), d13 = csub(a1, a3);
-                    // DIR i (a1 - a3)
-                    const float2 jd = DIR < 0 ? make_float2(d13.y, -d13.x) : make_float2(-d13.y, d13.x);
-                    const int k = n1 + 64 * (8 * g + i + h);
-                    y[0][h] = cadd(s02, s13);
-                    y[1][h] = cmul(cadd(d02, jd), root<DIR>(tw, 16384, k));
-                    y[2][h] = cmul(csub(s02, s13), root<DIR>(tw, 16384, (2 * k) & 16383));
-                    y[3][h] = cmul(csub(d02, jd), root<DIR>(tw, 16384, (3 * k) & 16383));
+            for (int m = 0; m < 4; ++m) {
+                float re[8], im[8];
+#pragma unroll
+                for (int i = 0; i < 8; ++i) {
+                    const float4 q = v[2 * i + (m >> 1)];
+                    re[i] = (m & 1) ? q.z : q.x;
+                    im[i] = (m & 1) ? q.w : q.y;
                 }
-#pragma unroll
-                for (int m = 0; m < 4; ++m) {
-                    uint32_t hr, lr, hi, li;
-                    HiLo<PREC>::pack(y[m][0].x, y[m][1].x, hr, lr);
-                    HiLo<PREC>::pack(y[m][0].y, y[m][1].y, hi, li);
-                    const uint32_t ore = gemm_off(m * 64 + n1, 8 * g + i), oim = gemm_off(m * 64 + n1, 64 + 8 * g + i);
-                    *reinterpret_cast<uint32_t *>(hp + ore) = hr;
-                    *reinterpret_cast<uint32_t *>(lp + ore) = lr;
-                    *reinterpret_cast<uint32_t *>(hp + oim) = hi;
-                    *reinterpret_cast<uint32_t *>(lp + oim) = li;
-                }
+                put_chunk<PREC>(hp, lp, gemm_off(m * 64 + n1, 8 * g), re);
+                put_chunk<PREC>(hp, lp, gemm_off(m * 64 + n1, 64 + 8 * g), im);
             }
         }
     };
@@ -349,9 +375,18 @@ __global__ void __launch_bounds__(kGemmBlock, 1)
     };
 
     // ---- D2 row (k1, part), columns = pass-2 operand rows of slot b -> X of
-    // `tile`: after the swap with the neighbour lane each thread holds eight
-    // consecutive outputs
+    // `tile`, staged in buffer b (free once pass 2 has completed) in output
+    // order, then copied out in whole lines.  Staging row: LOGN 12 (sub-signal,
+    // k1) of 64 outputs, LOGN 14 k1 of 256; the 16-byte units of a row are
+    // XOR-swizzled by (row % 4) * 2 so that the lanes of a quarter warp
+    // (four rows, two units each) hit eight different bank groups.
+    constexpr int ROWB = LOGN == 12 ? 512 : 2048;  // bytes per staging row
+    constexpr int UNITS = 2 * G::PLANE / 16;       // 16-byte units of a tile's output
+    auto stage_at = [&](int row, int unit) {
+        return row * ROWB + 16 * (unit ^ ((row & 3) << 1));
+    };
     auto epi2 = [&](int b, int64_t tile) {
+        unsigned char *stage = plane_hi(b);  // both planes, contiguous
         const int r = 32 * (warp & 3) + lane;
         const int k1 = r >> 1, odd = r & 1;
         constexpr int CPW = G::ROWS / 4;
@@ -362,90 +397,106 @@ __global__ void __launch_bounds__(kGemmBlock, 1)
             uint32_t raw[16];
             tmem_ld16(tmem + tq + kGemmFCols + static_cast<uint32_t>(b * G::SLOT_COLS + cb), raw);
             tmem_wait_ld();
-            const int rho = cb + 8 * odd;  // pass-2 operand rows rho .. rho + 7
+            // the even lane keeps columns cb + 4t + {0, 1}, the odd lane
+            // cb + 4t + {2, 3} (t = 0..3)
             float2 z[8];
 #pragma unroll
             for (int t = 0; t < 8; ++t) {
-                const uint32_t send = odd ? raw[t] : raw[8 + t];
+                const int mine = 4 * (t >> 1) + (t & 1);  // even lane's column; + 2 for the odd lane
+                const uint32_t send = odd ? raw[mine] : raw[mine + 2];
                 const float got = __uint_as_float(__shfl_xor_sync(kFullMask, send, 1));
-                z[t] = odd ? make_float2(got, __uint_as_float(raw[8 + t])) : make_float2(__uint_as_float(raw[t]), got);
+                z[t] = odd ? make_float2(got, __uint_as_float(raw[mine + 2])) : make_float2(__uint_as_float(raw[mine]), got);
             }
-            float4 *dst;
-            bool live = true;
-            if constexpr (LOGN == 12) {
-                const int64_t sig = tile * 2 + (rho >> 6);
-                live = sig < batch;
-                dst = reinterpret_cast<float4 *>(out + sig * N + 64 * k1 + (rho & 63));
-            } else {
-                dst = reinterpret_cast<float4 *>(out + tile * N + 256 * k1 + rho);
-            }
-            if (live) {
+            const int row = LOGN == 12 ? (cb >> 6) * 64 + k1 : k1;
+            const int unit0 = (LOGN == 12 ? (cb & 63) : cb) >> 1;
 #pragma unroll
-                for (int t = 0; t < 4; ++t)
-                    __stcs(dst + t, make_float4(z[2 * t].x, z[2 * t].y, z[2 * t + 1].x, z[2 * t + 1].y));
+            for (int t = 0; t < 4; ++t)
+                *reinterpret_cast<float4 *>(stage + stage_at(row, unit0 + 2 * t + odd)) =
+                    make_float4(z[2 * t].x, z[2 * t].y, z[2 * t + 1].x, z[2 * t + 1].y);
+        }
+        workers_sync();
+        float4 *dst = reinterpret_cast<float4 *>(out + tile * (G::SIG * N));
+        constexpr int UPR = ROWB / 16;  // units per row
+#pragma unroll
+        for (int j0 = 0; j0 < UNITS / kGemmThreads; j0 += 4) {
+            float4 w[4];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const int u = tid + kGemmThreads * (j0 + j);
+                w[j] = *reinterpret_cast<const float4 *>(stage + stage_at(u / UPR, u % UPR));
+            }
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const int u = tid + kGemmThreads * (j0 + j);
+                const bool live = LOGN == 12 ? tile * 2 + u / (UNITS / 2) < batch : true;
+                if (live) __stcs(dst + u, w[j]);
             }
         }
+        workers_sync();  // the buffer may be refilled
     };
 
-    // ---- the pipeline.  The workers fill a buffer, arrive on its `ready`
-    // barrier (after a proxy fence and a tensor-memory fence), and wait on its
-    // `done` barrier; the product warp waits on `ready`, issues the pass and
-    // commits it to `done`.  With two buffers, tile i + 1 is prepared and its
-    // pass 1 runs while tile i's pass 2 runs and is written out.
+    // ---- the pipeline.  The workers fill a buffer (or finish reading a
+    // slot) and arrive on its `ready` barrier after a proxy fence and a
+    // tensor-memory fence; the issuing warp (the 17th, or worker warp 0) then
+    // waits for `ready`, issues the pass from one lane and commits it to
+    // `done`, on which the workers wait before reading the result.  With two
+    // buffers, tile i + 1 is prepared and its pass 1 runs while tile i's pass
+    // 2 runs and is written out.  Every worker runs the same sequence of
+    // barriers whatever happens to `ok`.
     const int64_t stride = gridDim.x;
-    if (mma_warp) {
-        for (int64_t i = 0, tile = blockIdx.x; tile < ntiles && ok; ++i, tile += stride) {
+    if (G::ISSUER_WARP && warp == kGemmThreads / 32) {
+        for (int64_t i = 0, tile = blockIdx.x; tile < ntiles; ++i, tile += stride) {
             const int b = G::NBUF == 2 ? static_cast<int>(i & 1) : 0;
-            const uint64_t bh = gemm_desc(smem_u32(plane_hi(b))), bl = gemm_desc(smem_u32(plane_lo(b)));
-            for (int pass = 0; pass < 2 && ok; ++pass) {
-                ok = gemm_wait(&ready[b], ph_ready[b]);
+            for (int pass = 0; pass < 2; ++pass) {
+                gemm_wait(&ready[b], ph_ready[b], ok);
                 if (ok && lane == 0) {
                     tc_fence_after();
-                    issue(b, bh, bl);
+                    issue(b, gemm_desc(smem_u32(plane_hi(b))), gemm_desc(smem_u32(plane_lo(b))));
                 }
                 __syncwarp();
             }
         }
-    } else {
-        auto publish = [&](int b) {  // buffer b filled / slot b read by this warp
-            fence_proxy_async();
-            tc_fence_before();
+    }
+    auto publish = [&](int b) {
+        fence_proxy_async();
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&ready[b]);
+        if (!G::ISSUER_WARP && warp == 0) {
+            gemm_wait(&ready[b], ph_ready[b], ok);
+            if (ok && lane == 0) {
+                tc_fence_after();
+                issue(b, gemm_desc(smem_u32(plane_hi(b))), gemm_desc(smem_u32(plane_lo(b))));
+            }
             __syncwarp();
-            if (lane == 0) mbar_arrive(&ready[b]);
-        };
-        int64_t tile = blockIdx.x;
-        if (tile < ntiles) {
-            load(tile);
-            prep(0);
-            publish(0);
-            if (tile + stride < ntiles) load(tile + stride);
         }
-        for (int64_t i = 0; tile < ntiles; ++i, tile += stride) {
-            const int cur = G::NBUF == 2 ? static_cast<int>(i & 1) : 0;
-            const bool more = tile + stride < ntiles;
-            if (!gemm_wait(&done[cur], ph_done[cur])) {  // pass 1 of this tile
-                ok = false;
-                break;
-            }
-            tc_fence_after();
-            epi1(cur);
-            publish(cur);
-            if (G::NBUF == 2 && more) {
-                prep(cur ^ 1);
-                publish(cur ^ 1);
-                if (tile + 2 * stride < ntiles) load(tile + 2 * stride);
-            }
-            if (!gemm_wait(&done[cur], ph_done[cur])) {  // pass 2 of this tile
-                ok = false;
-                break;
-            }
-            tc_fence_after();
-            epi2(cur, tile);
-            if (G::NBUF == 1 && more) {
-                prep(0);
-                publish(0);  // also releases the slot read by epi2
-                if (tile + 2 * stride < ntiles) load(tile + 2 * stride);
-            }
+    };
+    int64_t tile = G::ISSUER_WARP && warp == kGemmThreads / 32 ? ntiles : blockIdx.x;
+    if (tile < ntiles) {
+        load(tile);
+        prep(0);
+        publish(0);
+        if (tile + stride < ntiles) load(tile + stride);
+    }
+    for (int64_t i = 0; tile < ntiles; ++i, tile += stride) {
+        const int cur = G::NBUF == 2 ? static_cast<int>(i & 1) : 0;
+        const bool more = tile + stride < ntiles;
+        gemm_wait(&done[cur], ph_done[cur], ok);  // pass 1 of this tile
+        tc_fence_after();
+        epi1(cur);
+        publish(cur);
+        if (G::NBUF == 2 && more) {
+            prep(cur ^ 1);
+            publish(cur ^ 1);
+            if (tile + 2 * stride < ntiles) load(tile + 2 * stride);
+        }
+        gemm_wait(&done[cur], ph_done[cur], ok);  // pass 2 of this tile
+        tc_fence_after();
+        epi2(cur, tile);
+        if (G::NBUF == 1 && more) {
+            prep(0);
+            publish(0);  // also releases the slot read by epi2
+            if (tile + 2 * stride < ntiles) load(tile + 2 * stride);
         }
     }
 
@@ -477,6 +528,8 @@ const void *fft_tc_gemm_func(int prec, int dir, int logn) {
 
 int fft_tc_gemm_smem(int logn) { return logn == 12 ? gemm_smem_bytes<12>() : gemm_smem_bytes<14>(); }
 
+int fft_tc_gemm_threads(int logn) { return logn == 12 ? GemmShape<12>::BLOCK : GemmShape<14>::BLOCK; }
+
 // persistent launch: one block per SM at most, tiles of two 4096-point
 // signals or one 16384-point signal
 int fft_tc_gemm_launch(const void *func, const void *in, void *out, int64_t n, int64_t batch, cudaStream_t s) {
@@ -489,12 +542,13 @@ int fft_tc_gemm_launch(const void *func, const void *in, void *out, int64_t n, i
     if (rc != BPLG_OK) return rc;
     const int64_t ntiles = logn == 12 ? (batch + 1) / 2 : batch;
     int64_t grid = 0;
-    rc = persistent_grid(func, kGemmBlock, smem, ntiles, &grid);
+    const int threads = fft_tc_gemm_threads(logn);
+    rc = persistent_grid(func, threads, smem, ntiles, &grid);
     if (rc != BPLG_OK) return rc;
     void *args[] = {(void *)&in, (void *)&out, (void *)&tw, &batch};
-    cudaError_t e = cudaLaunchKernel(func, dim3(static_cast<unsigned>(grid)), dim3(kGemmBlock), args,
+    cudaError_t e = cudaLaunchKernel(func, dim3(static_cast<unsigned>(grid)), dim3(threads), args,
                                      static_cast<size_t>(smem), s);
-    return e == cudaSuccess ? BPLG_OK : launch_error(e, "fft tc (two GEMM passes) launch", func, grid, kGemmBlock, smem);
+    return e == cudaSuccess ? BPLG_OK : launch_error(e, "fft tc (two GEMM passes) launch", func, grid, threads, smem);
 }
 
 // Read (and optionally clear) the device error word of this file's kernel
