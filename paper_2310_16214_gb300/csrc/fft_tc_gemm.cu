@@ -29,17 +29,27 @@
 // swaps halves with its neighbour lane (rows 2k and 2k + 1 hold the real
 // and imaginary parts), applies the twiddles in float32 (from the
 // float64-generated table, kept in shared memory), splits and writes its row
-// of A2 into the same buffer.  After pass 2 the same swap leaves each thread
-// eight consecutive outputs, written with 16-byte stores.
+// of A2 into the same buffer.  After pass 2 the same swap leaves each pair
+// of lanes sixteen consecutive outputs.
 //
-// Blocks are persistent (one per SM, 512 threads, 160 KB of shared memory,
-// 512 tensor-memory columns) and load the next tile -- two 4096-point
-// signals or one 16384-point signal -- into registers while the tensor cores
-// run the current one.  For 4096 points two tiles are in flight, with two
-// data buffers and two tensor-memory slots: tile i + 1 is prepared and its
-// pass 1 runs while tile i's pass 2 runs and is written out.  Waits on the
-// MMA barriers are bounded: on a timeout the block records the device error
-// word and stops.
+// Blocks are persistent (one per SM, 512 worker threads) and load the next
+// tile -- two 4096-point signals or one 16384-point signal -- into
+// registers while the tensor cores run the current one.  The workers fill a
+// buffer and arrive on an mbarrier; one thread waits on it, issues the
+// products and commits them to a second mbarrier, on which the workers wait.
+//   4096 points: a 17th warp issues.  Two tiles are in flight, with two data
+//     buffers and two tensor-memory slots: tile i + 1 is prepared and its
+//     pass 1 runs while tile i's pass 2 runs and is written out, through the
+//     freed buffer, in whole lines.
+//   16384 points: one lane of worker warp 0 issues (a 17th warp would cap
+//     the registers at 96, too few for the prefetched tile).  A tile runs in
+//     halves (quarters 0-1 and 2-3 of the radix-4 output), each pass as two
+//     products of N = 128, so the CUDA cores work on one half while the
+//     tensor cores run the other; the halves of D rotate through three
+//     128-column blocks of tensor memory, so that the next tile's first
+//     product runs while this tile's output is read and written.
+// Waits on the barriers are bounded: on a timeout the block records the
+// device error word and runs on without waiting, through the same barriers.
 #include "device_util.cuh"
 #include "fft_common.cuh"
 #include "internal.h"
@@ -85,17 +95,21 @@ struct GemmShape {
 };
 
 // tensor memory: F at columns 0..127 (hi planes 0..63, lo 64..127, two
-// 16-bit K elements per column), then NBUF slots of D
+// 16-bit K elements per column), then NBUF slots of D (4096 points), or
+// three blocks of 128 columns that the halves of D rotate through (16384
+// points)
 constexpr uint32_t kGemmTmemCols = 512;
 constexpr uint32_t kGemmFCols = 128;
 
-// shared memory: the twiddles W4096^(n1 k2) (64 rows of 65, the pad
-// keeping rows 8 apart on other banks) and NBUF data buffers of two planes
-// each (at a 1 KB boundary)
+// shared memory: the twiddles W4096^(n1 k2) between the passes (64 rows of
+// 65, the pad keeping rows 8 apart on other banks), then NBUF data buffers
+// of two planes each.  16384 points add the 3 x 64 tables W16384^(m n1) and
+// W256^(m n2), m = 1..3, whose product is the radix-4 twiddle W16384^(m k),
+// k = n1 + 64 n2.  (Shared memory is kept well below the maximum: what is
+// left is the L1 cache, and the loads of the next tile, up to 128 KB in
+// flight per SM, need it.)
 constexpr int kTwStride = 65;
-constexpr int kTwBytes = (64 * kTwStride * 8 + 1023) / 1024 * 1024;
-// 16384 points: the radix-4 stage's twiddle W16384^(m k), k = n1 + 64 n2,
-// as the product W16384^(m n1) W256^(m n2) of two 3 x 64 tables
+constexpr int kTwBytes = 64 * kTwStride * 8;
 constexpr int kTw14Bytes = 2 * 3 * 64 * 8;
 template <int LOGN>
 constexpr int gemm_smem_bytes() {
@@ -121,6 +135,13 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
           "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
         : "r"(taddr)
         : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld4(uint32_t taddr, uint32_t *r) {
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0, %1, %2, %3}, [%4];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+                 : "r"(taddr)
+                 : "memory");
 }
 
 // W_m^e = exp(DIR 2 pi i e / m) from the table of exp(-2 pi i e / m)
@@ -174,15 +195,15 @@ __global__ void __launch_bounds__(GemmShape<LOGN>::BLOCK, 1)
                        int64_t batch) {
     using G = GemmShape<LOGN>;
     constexpr int N = 1 << LOGN;
-    extern __shared__ __align__(1024) unsigned char smem[];
+    extern __shared__ __align__(128) unsigned char smem[];
     float2 *tws = reinterpret_cast<float2 *>(smem);  // [n1][k2], rows kTwStride apart
     unsigned char *dbuf = smem + kTwBytes;           // buffer b: hi plane, lo plane
     // 16384 points: W16384^(m n1) at [m - 1][n1], W256^(m n2) at [3 + m - 1][n2]
-    float2 *tw14 = reinterpret_cast<float2 *>(dbuf + G::NBUF * 2 * G::PLANE);
+    float2 *tw14 = reinterpret_cast<float2 *>(dbuf + G::NBUF * 2 * G::PLANE);  // 16384 points
     // ready[b]: the workers have filled buffer b (and are done reading slot
     // b); done[b]: the products over buffer b have completed
-    __shared__ __align__(8) uint64_t ready[G::NBUF];
-    __shared__ __align__(8) uint64_t done[G::NBUF];
+    __shared__ __align__(8) uint64_t ready[2];
+    __shared__ __align__(8) uint64_t done[2];
     __shared__ uint32_t tmem_slot;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int64_t ntiles = (batch + G::SIG - 1) / G::SIG;
@@ -193,7 +214,7 @@ __global__ void __launch_bounds__(GemmShape<LOGN>::BLOCK, 1)
     }
     if (tid == 0) {
 #pragma unroll
-        for (int b = 0; b < G::NBUF; ++b) {
+        for (int b = 0; b < 2; ++b) {
             mbar_init(&ready[b], kGemmThreads / 32);  // one arrival per worker warp
             mbar_init(&done[b], 1);
         }
@@ -240,9 +261,9 @@ __global__ void __launch_bounds__(GemmShape<LOGN>::BLOCK, 1)
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
-    uint32_t ph_ready[G::NBUF], ph_done[G::NBUF];
+    uint32_t ph_ready[2], ph_done[2];
 #pragma unroll
-    for (int b = 0; b < G::NBUF; ++b) ph_ready[b] = ph_done[b] = 0u;
+    for (int b = 0; b < 2; ++b) ph_ready[b] = ph_done[b] = 0u;
     bool ok = true;
 
     auto plane_hi = [&](int b) { return dbuf + b * 2 * G::PLANE; };
@@ -272,6 +293,47 @@ __global__ void __launch_bounds__(GemmShape<LOGN>::BLOCK, 1)
         }
     };
 
+    // ---- 16384 points: the radix-4 first stage in place (v[2i] <- y0, y1
+    // and v[2i + 1] <- y2, y3 of n2 = 8g + i, g = tid / 64, n1 = tid % 64)
+    auto radix4 = [&]() {
+        const int g = tid >> 6, n1 = tid & 63;
+        const float2 w1 = tw14[n1], w2 = tw14[64 + n1], w3 = tw14[128 + n1];  // W16384^(m n1)
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            const float4 p01 = v[2 * i], p23 = v[2 * i + 1];
+            const float2 a0 = make_float2(p01.x, p01.y), a1 = make_float2(p01.z, p01.w);
+            const float2 a2 = make_float2(p23.x, p23.y), a3 = make_float2(p23.z, p23.w);
+            const float2 s02 = cadd(a0, a2), d02 = csub(a0, a2), s13 = cadd(a1, a3), d13 = csub(a1, a3);
+            // DIR i (a1 - a3)
+            const float2 jd = DIR < 0 ? make_float2(d13.y, -d13.x) : make_float2(-d13.y, d13.x);
+            const int n2 = 8 * g + i;  // W256^(m n2)
+            const float2 y0 = cadd(s02, s13);
+            const float2 y1 = cmul(cadd(d02, jd), cmul(w1, tw14[3 * 64 + n2]));
+            const float2 y2 = cmul(csub(s02, s13), cmul(w2, tw14[4 * 64 + n2]));
+            const float2 y3 = cmul(csub(d02, jd), cmul(w3, tw14[5 * 64 + n2]));
+            v[2 * i] = make_float4(y0.x, y0.y, y1.x, y1.y);
+            v[2 * i + 1] = make_float4(y2.x, y2.y, y3.x, y3.y);
+        }
+    };
+    // pass-1 operand rows m * 64 + n1 of quarters m = m0, m0 + 1: the
+    // thread's eight consecutive n2 form one 16-byte chunk per plane and part
+    auto put_quarters = [&](int b, int m0) {
+        unsigned char *hp = plane_hi(b), *lp = plane_lo(b);
+        const int g = tid >> 6, n1 = tid & 63;
+#pragma unroll
+        for (int m = m0; m < m0 + 2; ++m) {
+            float re[8], im[8];
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                const float4 q = v[2 * i + (m >> 1)];
+                re[i] = (m & 1) ? q.z : q.x;
+                im[i] = (m & 1) ? q.w : q.y;
+            }
+            put_chunk<PREC>(hp, lp, gemm_off(m * 64 + n1, 8 * g), re);
+            put_chunk<PREC>(hp, lp, gemm_off(m * 64 + n1, 64 + 8 * g), im);
+        }
+    };
+
     // ---- pass-1 operand of the loaded tile: row (sub-signal, n1), K = [re n2 | im n2]
     auto prep = [&](int b) {
         unsigned char *hp = plane_hi(b), *lp = plane_lo(b);
@@ -295,40 +357,9 @@ __global__ void __launch_bounds__(GemmShape<LOGN>::BLOCK, 1)
                 put_chunk<PREC>(hp, lp, gemm_off(row, 64 + 8 * g), im);
             }
         } else {
-            // radix-4 first stage in place (v[2i] <- y0, y1 and v[2i + 1] <-
-            // y2, y3 of n2 = 8g + i); then for each output quarter m the
-            // thread's eight consecutive n2 form one 16-byte chunk per plane
-            // and part
-            const int g = tid >> 6, n1 = tid & 63;
-            const float2 w1 = tw14[n1], w2 = tw14[64 + n1], w3 = tw14[128 + n1];  // W16384^(m n1)
-#pragma unroll
-            for (int i = 0; i < 8; ++i) {
-                const float4 p01 = v[2 * i], p23 = v[2 * i + 1];
-                const float2 a0 = make_float2(p01.x, p01.y), a1 = make_float2(p01.z, p01.w);
-                const float2 a2 = make_float2(p23.x, p23.y), a3 = make_float2(p23.z, p23.w);
-                const float2 s02 = cadd(a0, a2), d02 = csub(a0, a2), s13 = cadd(a1, a3), d13 = csub(a1, a3);
-                // DIR i (a1 - a3)
-                const float2 jd = DIR < 0 ? make_float2(d13.y, -d13.x) : make_float2(-d13.y, d13.x);
-                const int n2 = 8 * g + i;  // W256^(m n2)
-                const float2 y0 = cadd(s02, s13);
-                const float2 y1 = cmul(cadd(d02, jd), cmul(w1, tw14[3 * 64 + n2]));
-                const float2 y2 = cmul(csub(s02, s13), cmul(w2, tw14[4 * 64 + n2]));
-                const float2 y3 = cmul(csub(d02, jd), cmul(w3, tw14[5 * 64 + n2]));
-                v[2 * i] = make_float4(y0.x, y0.y, y1.x, y1.y);
-                v[2 * i + 1] = make_float4(y2.x, y2.y, y3.x, y3.y);
-            }
-#pragma unroll
-            for (int m = 0; m < 4; ++m) {
-                float re[8], im[8];
-#pragma unroll
-                for (int i = 0; i < 8; ++i) {
-                    const float4 q = v[2 * i + (m >> 1)];
-                    re[i] = (m & 1) ? q.z : q.x;
-                    im[i] = (m & 1) ? q.w : q.y;
-                }
-                put_chunk<PREC>(hp, lp, gemm_off(m * 64 + n1, 8 * g), re);
-                put_chunk<PREC>(hp, lp, gemm_off(m * 64 + n1, 64 + 8 * g), im);
-            }
+            radix4();
+            put_quarters(b, 0);
+            put_quarters(b, 2);
         }
     };
 
@@ -339,21 +370,32 @@ __global__ void __launch_bounds__(GemmShape<LOGN>::BLOCK, 1)
                   umma_idesc_f16(HiLo<PREC>::kFmt, 128, G::ROWS));
         umma_commit(&done[b]);
     };
+    // 16384 points: half hf of a pass, operand rows 128 hf .. 128 hf + 127,
+    // into tensor-memory block blk, committed to done[hf]
+    auto issue_half = [&](int hf, int blk) {
+        const uint64_t off = static_cast<uint64_t>(hf) * (gemm_off(128, 0) >> 4);
+        gemm_pass(tmem + kGemmFCols + static_cast<uint32_t>(128 * blk), tmem,
+                  gemm_desc(smem_u32(plane_hi(0))) + off, gemm_desc(smem_u32(plane_lo(0))) + off,
+                  umma_idesc_f16(HiLo<PREC>::kFmt, 128, 128));
+        umma_commit(&done[hf]);
+    };
 
     // ---- D1 row (k2, part), columns (sub-signal, n1) -> twiddled A2 rows in buffer b
-    auto epi1 = [&](int b) {
+    // (16384 points: half hf, quarters 2 hf and 2 hf + 1, in block blk)
+    auto epi1 = [&](int b, int hf = 0, int blk = 0) {
         unsigned char *hp = plane_hi(b), *lp = plane_lo(b);
         const int r = 32 * (warp & 3) + lane;  // D1 row of this thread
         const int k2 = r >> 1, odd = r & 1;
-        constexpr int CPW = G::ROWS / 4;  // columns per warp: each lane quarter is read by 4 warps
+        constexpr int CPW = 32;  // columns per warp: each lane quarter is read by 4 warps
         const int c0 = CPW * (warp >> 2);
+        const uint32_t cbase = LOGN == 12 ? static_cast<uint32_t>(b * G::SLOT_COLS) : static_cast<uint32_t>(128 * blk);
 #pragma unroll
         for (int h = 0; h < CPW / 16; ++h) {
             const int cb = c0 + 16 * h;  // 16 columns of one sub-signal
             uint32_t raw[16];
-            tmem_ld16(tmem + tq + kGemmFCols + static_cast<uint32_t>(b * G::SLOT_COLS + cb), raw);
+            tmem_ld16(tmem + tq + kGemmFCols + cbase + static_cast<uint32_t>(cb), raw);
             tmem_wait_ld();
-            const int u = cb >> 6;
+            const int u = 2 * hf + (cb >> 6);
             const int nb = (cb & 63) + 8 * odd;  // this thread keeps n1 = nb .. nb + 7
             float re[8], im[8];
 #pragma unroll
@@ -366,27 +408,25 @@ __global__ void __launch_bounds__(GemmShape<LOGN>::BLOCK, 1)
                 re[t] = zt.x;
                 im[t] = zt.y;
             }
-            // pass-2 operand row: (sub-signal, k2), sub-signal fastest for
-            // 16384 points (whose outputs X[4 (k2 + 64 k1) + u] interleave)
-            const int row = LOGN == 12 ? u * 64 + k2 : 4 * k2 + u;
+            const int row = u * 64 + k2;  // pass-2 operand row (sub-signal, k2)
             put_chunk<PREC>(hp, lp, gemm_off(row, nb), re);
             put_chunk<PREC>(hp, lp, gemm_off(row, 64 + nb), im);
         }
     };
 
-    // ---- D2 row (k1, part), columns = pass-2 operand rows of slot b -> X of
-    // `tile`, staged in buffer b (free once pass 2 has completed) in output
-    // order, then copied out in whole lines.  Staging row: LOGN 12 (sub-signal,
-    // k1) of 64 outputs, LOGN 14 k1 of 256; the 16-byte units of a row are
-    // XOR-swizzled by (row % 4) * 2 so that the lanes of a quarter warp
-    // (four rows, two units each) hit eight different bank groups.
-    constexpr int ROWB = LOGN == 12 ? 512 : 2048;  // bytes per staging row
+    // ---- D2 row (k1, part), columns = pass-2 operand rows -> X of `tile`.
+    // 4096 points: staged in buffer b (free once pass 2 has completed) in
+    // output order, then copied out in whole lines; staging row (sub-signal,
+    // k1) of 64 outputs, its 16-byte units XOR-swizzled by (row % 4) * 2 so
+    // that the lanes of a quarter warp (four rows, two units each) hit eight
+    // different bank groups.  16384 points: written directly.
+    constexpr int ROWB = 512;                      // bytes per staging row
     constexpr int UNITS = 2 * G::PLANE / 16;       // 16-byte units of a tile's output
-    auto stage_at = [&](int row, int unit) {
-        return row * ROWB + 16 * (unit ^ ((row & 3) << 1));
+    auto stage_at = [&](int b, int row, int unit) {
+        return plane_hi(b) + row * ROWB + 16 * (unit ^ ((row & 3) << 1));  // both planes, contiguous
     };
-    auto epi2 = [&](int b, int64_t tile) {
-        unsigned char *stage = plane_hi(b);  // both planes, contiguous
+    // (16384 points: quarters 0-1 in block blk_a, 2-3 in blk_b)
+    auto epi2 = [&](int b, int64_t tile, int blk_a = 0, int blk_b = 0) {
         const int r = 32 * (warp & 3) + lane;
         const int k1 = r >> 1, odd = r & 1;
         constexpr int CPW = G::ROWS / 4;
@@ -394,26 +434,50 @@ __global__ void __launch_bounds__(GemmShape<LOGN>::BLOCK, 1)
 #pragma unroll
         for (int h = 0; h < CPW / 16; ++h) {
             const int cb = c0 + 16 * h;
+            // x[p], p = 0..15: sixteen consecutive outputs of this lane's part
+            // (4096 points: columns cb + p; 16384 points: X[4 (kb + j) + u] =
+            // column 64 u + kb + j, p = 4 j + u, kb = cb / 4)
             uint32_t raw[16];
-            tmem_ld16(tmem + tq + kGemmFCols + static_cast<uint32_t>(b * G::SLOT_COLS + cb), raw);
+            if constexpr (LOGN == 12) {
+                tmem_ld16(tmem + tq + kGemmFCols + static_cast<uint32_t>(b * G::SLOT_COLS + cb), raw);
+            } else {
+#pragma unroll
+                for (int u = 0; u < 4; ++u)
+                    tmem_ld4(tmem + tq + kGemmFCols +
+                                 static_cast<uint32_t>(128 * (u < 2 ? blk_a : blk_b) + 64 * (u & 1) + cb / 4),
+                             &raw[4 * u]);
+            }
             tmem_wait_ld();
-            // the even lane keeps columns cb + 4t + {0, 1}, the odd lane
-            // cb + 4t + {2, 3} (t = 0..3)
+            auto x = [&](int p) { return LOGN == 12 ? raw[p] : raw[4 * (p & 3) + (p >> 2)]; };
+            // the even lane keeps outputs p = 4t + {0, 1}, the odd lane
+            // 4t + {2, 3} (t = 0..3)
             float2 z[8];
 #pragma unroll
             for (int t = 0; t < 8; ++t) {
-                const int mine = 4 * (t >> 1) + (t & 1);  // even lane's column; + 2 for the odd lane
-                const uint32_t send = odd ? raw[mine] : raw[mine + 2];
+                const int mine = 4 * (t >> 1) + (t & 1);  // even lane's output; + 2 for the odd lane
+                const uint32_t send = odd ? x(mine) : x(mine + 2);
                 const float got = __uint_as_float(__shfl_xor_sync(kFullMask, send, 1));
-                z[t] = odd ? make_float2(got, __uint_as_float(raw[mine + 2])) : make_float2(__uint_as_float(raw[mine]), got);
+                z[t] = odd ? make_float2(got, __uint_as_float(x(mine + 2))) : make_float2(__uint_as_float(x(mine)), got);
             }
-            const int row = LOGN == 12 ? (cb >> 6) * 64 + k1 : k1;
-            const int unit0 = (LOGN == 12 ? (cb & 63) : cb) >> 1;
+            if constexpr (LOGN == 14) {
+                // written directly (the buffer already holds the next tile's
+                // quarters 0-1): each pair of lanes fills one 32-byte sector
+                // per store
+                float2 *dst = out + tile * N + 256 * k1 + cb + 2 * odd;
+#pragma unroll
+                for (int t = 0; t < 4; ++t)
+                    __stcs(reinterpret_cast<float4 *>(dst + 4 * t),
+                           make_float4(z[2 * t].x, z[2 * t].y, z[2 * t + 1].x, z[2 * t + 1].y));
+                continue;
+            }
+            const int row = (cb >> 6) * 64 + k1;  // (sub-signal, k1)
+            const int unit0 = (cb & 63) >> 1;
 #pragma unroll
             for (int t = 0; t < 4; ++t)
-                *reinterpret_cast<float4 *>(stage + stage_at(row, unit0 + 2 * t + odd)) =
+                *reinterpret_cast<float4 *>(stage_at(b, row, unit0 + 2 * t + odd)) =
                     make_float4(z[2 * t].x, z[2 * t].y, z[2 * t + 1].x, z[2 * t + 1].y);
         }
+        if constexpr (LOGN == 14) return;
         workers_sync();
         float4 *dst = reinterpret_cast<float4 *>(out + tile * (G::SIG * N));
         constexpr int UPR = ROWB / 16;  // units per row
@@ -423,7 +487,7 @@ __global__ void __launch_bounds__(GemmShape<LOGN>::BLOCK, 1)
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
                 const int u = tid + kGemmThreads * (j0 + j);
-                w[j] = *reinterpret_cast<const float4 *>(stage + stage_at(u / UPR, u % UPR));
+                w[j] = *reinterpret_cast<const float4 *>(stage_at(b, u / UPR, u % UPR));
             }
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
@@ -471,7 +535,66 @@ __global__ void __launch_bounds__(GemmShape<LOGN>::BLOCK, 1)
             __syncwarp();
         }
     };
-    int64_t tile = G::ISSUER_WARP && warp == kGemmThreads / 32 ? ntiles : blockIdx.x;
+    // 16384 points, in halves (quarters 0-1 and 2-3 of the radix-4 stage's
+    // output): pass 1 over quarters 0-1 runs while 2-3 are stored, pass 1
+    // over 2-3 while the first half of its output is twiddled, and so on.
+    // Tile i's halves of D use tensor-memory blocks 2i mod 3 and 2i + 1 mod 3,
+    // so that pass 1 over the next tile's quarters 0-1 runs (in the third
+    // block, from the first halves of the planes) while this tile's output
+    // is read and staged.
+    auto publish_half = [&](int hf, int blk) {
+        fence_proxy_async();
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&ready[hf]);
+        if (warp == 0) {
+            gemm_wait(&ready[hf], ph_ready[hf], ok);
+            if (ok && lane == 0) {
+                tc_fence_after();
+                issue_half(hf, blk);
+            }
+            __syncwarp();
+        }
+    };
+    if constexpr (LOGN == 14) {
+        int64_t tile = blockIdx.x;
+        if (tile < ntiles) {
+            load(tile);
+            radix4();
+            put_quarters(0, 0);
+            publish_half(0, 0);
+            put_quarters(0, 2);
+            publish_half(1, 1);
+            if (tile + stride < ntiles) load(tile + stride);
+        }
+        for (int i = 0; tile < ntiles; ++i, tile += stride) {
+            const bool more = tile + stride < ntiles;
+            const int blk_a = (2 * i) % 3, blk_b = (2 * i + 1) % 3, blk_next = (2 * i + 2) % 3;
+            gemm_wait(&done[0], ph_done[0], ok);  // pass 1, quarters 0-1
+            tc_fence_after();
+            epi1(0, 0, blk_a);
+            publish_half(0, blk_a);
+            gemm_wait(&done[1], ph_done[1], ok);  // pass 1, quarters 2-3
+            tc_fence_after();
+            epi1(0, 1, blk_b);
+            publish_half(1, blk_b);
+            gemm_wait(&done[0], ph_done[0], ok);  // pass 2, first half: rows 0..127 free
+            if (more) {
+                radix4();
+                put_quarters(0, 0);
+                publish_half(0, blk_next);
+            }
+            gemm_wait(&done[1], ph_done[1], ok);  // pass 2, second half
+            tc_fence_after();
+            epi2(0, tile, blk_a, blk_b);
+            if (more) {
+                put_quarters(0, 2);
+                publish_half(1, blk_a);  // block blk_a was read by epi2
+                if (tile + 2 * stride < ntiles) load(tile + 2 * stride);
+            }
+        }
+    }
+    int64_t tile = LOGN == 14 || (G::ISSUER_WARP && warp == kGemmThreads / 32) ? ntiles : blockIdx.x;
     if (tile < ntiles) {
         load(tile);
         prep(0);
@@ -506,7 +629,7 @@ __global__ void __launch_bounds__(GemmShape<LOGN>::BLOCK, 1)
     // memory is freed (bounded)
     if (!__syncthreads_and(ok) && tid == 0) {
 #pragma unroll
-        for (int b = 0; b < G::NBUF; ++b) mbar_wait_bounded(&done[b], ph_done[b]);
+        for (int b = 0; b < 2; ++b) mbar_wait_bounded(&done[b], ph_done[b]);
     }
     if (warp == 0) tmem_dealloc(tmem, kGemmTmemCols);
 }
