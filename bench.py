@@ -537,6 +537,12 @@ def run_ours(args):
             tuning = tuning_quality(bp, wl)
         except Exception as exc:  # reported, never fatal to the bench line
             tuning = {"unavailable": str(exc)[:200]}
+    precision = None
+    if rank == 0 and not args.no_precision:
+        try:
+            precision = precision_quality(bp, torch, peak)
+        except Exception as exc:  # reported, never fatal to the bench line
+            precision = {"unavailable": str(exc)[:200]}
 
     if rank == 0:
         line = {
@@ -551,7 +557,7 @@ def run_ours(args):
                        "parallelism": "replicas" if world > 1 else "single"},
             "roofline": roofline, "per_op": per_op, "per_launch": items_out,
             "gpu_launches": launches_per_step * args.steps, "clocks": clocks, "refined_corrections": refined_iters,
-            "e2e": e2e, "cpu_baseline": cpu, "external": ext, "tuning": tuning,
+            "e2e": e2e, "cpu_baseline": cpu, "external": ext, "tuning": tuning, "precision": precision,
         }
         print(json.dumps(line))
     if world > 1:
@@ -617,6 +623,67 @@ def tuning_quality(bp, wl, reps: int = 30):
                       "model = BPLG_TUNE_MODEL (GB300 cost model, 0 evaluations), analytic = the paper's guideline "
                       "(0 evaluations), learned = the plans the timed step ran (Bayesian optimisation, budget 40)"
                       % reps}
+
+
+def precision_quality(bp, torch, peak, reps: int = 10, check_rows: int = 32):
+    """The precision configuration's FFT rows (N = 2^10, 2^12, 2^14, batch
+    2^26 / N, seeded U[-1, 1] data): the float32 CUDA-core path against the
+    tensor-core path with BF16 and FP16 split operands, forward transforms.
+    Float32 runs its default plan (the GB300 cost model's); each tensor-core
+    precision runs the fastest of its enumerated plans (median of `reps`
+    launches each), whose error is checked on `check_rows` sampled signals
+    against numpy's float64 FFT (relative L2 per signal; tolerance
+    1e-5 log2 N)."""
+    t0 = time.time()
+    st = torch.cuda.current_stream()
+
+    def timed(fn, r):
+        for _ in range(2):
+            fn()
+        ev = []
+        for _ in range(r):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(st)
+            fn()
+            e1.record(st)
+            ev.append((e0, e1))
+        torch.cuda.synchronize()
+        return statistics.median(a.elapsed_time(b) for a, b in ev)
+
+    out = {}
+    for n in (1 << 10, 1 << 12, 1 << 14):
+        batch = (1 << 26) // n
+        z = si.fft_c64(batch, n, seed=si.CONFIG_SEEDS["precision"], stream=n)
+        zd = torch.from_numpy(z.view(np.float32).reshape(-1)).cuda()
+        od = torch.empty_like(zd)
+        rows = np.unique(np.random.default_rng(5).integers(0, batch, check_rows))
+        ref = np.fft.fft(z[rows].astype(np.complex128), axis=1)
+
+        def err():
+            X = od.view(-1, 2 * n)[torch.from_numpy(rows).cuda()].cpu().numpy().view(np.complex64)
+            e = np.linalg.norm(X.astype(np.complex128) - ref, axis=1) / np.linalg.norm(ref, axis=1)
+            return float("%.3e" % e.max())
+
+        gb = 16 * n * batch / 1e9
+        row = {"batch": batch, "tolerance": round(1e-5 * math.log2(n), 6)}
+        ms = timed(lambda: bp.fft_batched(zd, od, n, batch, -1), reps)
+        row["fp32"] = {"ms": round(ms, 5), "hbm_frac": round(gb / (ms * 1e-3) / peak, 4), "err_max": err()}
+        plans = bp.enumerate_plans(bp.OP_FFT_TC, bp.F32, n)
+        for name, prec in (("tc_bf16", bp.TC_BF16), ("tc_f16", bp.TC_F16)):
+            best = None
+            for p in plans:
+                t = timed(lambda: bp.fft_tc_batched(zd, od, n, batch, -1, prec, plan=p), 3)
+                if best is None or t < best[0]:
+                    best = (t, p)
+            p = best[1]
+            ms = timed(lambda: bp.fft_tc_batched(zd, od, n, batch, -1, prec, plan=p), reps)
+            row[name] = {"ms": round(ms, 5), "hbm_frac": round(gb / (ms * 1e-3) / peak, 4), "err_max": err(),
+                         "plans_timed": len(plans),
+                         "plan": {k: v for k, v in p.as_dict().items() if k in ("P", "L", "spb", "io")}}
+        row["tc_over_fp32_speed"] = {k: round(row["fp32"]["ms"] / row[k]["ms"], 3) for k in ("tc_bf16", "tc_f16")}
+        out[str(n)] = row
+    out["seconds"] = round(time.time() - t0, 1)
+    return out
 
 
 def external_refs(torch, per_item, peak, reps: int = 20):
@@ -1156,12 +1223,11 @@ def nonpow2_report(args):
 def precision_report(args):
     """Precision configuration: FFT N in {2^10, 2^12, 2^14}, batch 2^26/N,
     tensor-core radix-16 stages with BF16 and FP16 split operands against
-    the float32 CUDA-core Stockham path; error against the float64 oracle on
-    sampled signals (max and median relative L2) and the median time of
+    the float32 CUDA-core Stockham path; error against numpy's float64 FFT
+    on sampled signals (max and median relative L2) and the median time of
     `reps` launches (plans: learned tuner for each path)."""
     import torch
     torch.cuda.set_device(0)
-    import oracle
     import paper_2310_16214_gb300 as bp
     peak, _ = read_peaks()
     out = []
@@ -1172,7 +1238,7 @@ def precision_report(args):
         od = torch.empty_like(zd)
         rng = np.random.default_rng(3)
         rows = np.unique(rng.integers(0, batch, 64))
-        ref = oracle.fft(z[rows], -1)
+        ref = np.fft.fft(z[rows].astype(np.complex128), axis=1)
         st = torch.cuda.current_stream()
         paths = {
             "fp32": (bp.OP_FFT, lambda p: bp.fft_batched(zd, od, n, batch, -1, plan=p)),
@@ -1219,6 +1285,8 @@ def main():
     ap.add_argument("--no-ext", action="store_true", help="skip the cuFFT / CUB / cuSPARSE references")
     ap.add_argument("--no-tuning", action="store_true",
                     help="skip the tuned-vs-exhaustive (Phi) measurement after the timed region")
+    ap.add_argument("--no-precision", action="store_true",
+                    help="skip the tensor-core vs float32 FFT comparison after the timed region")
     ap.add_argument("--tune-report", action="store_true", help="tuned vs exhaustive Phi report instead of the bench")
     ap.add_argument("--precision-report", action="store_true",
                     help="tensor-core (BF16/FP16 split) vs float32 FFT: error and time per N")

@@ -301,6 +301,7 @@ struct ModelOp {
     double acc = 0;     // warp-wide global access instructions per thread
     double lines = 1;   // 128-byte lines per such access
     bool piped = false; // bulk-copy ring in front of the loads
+    bool persistent = false;  // one block per SM looping over tiles, the next tile's loads in flight
     double fp64 = 0;    // FP64 pipe operations per element
 };
 
@@ -336,14 +337,16 @@ ModelOp model_op(const bplg_plan &p, int64_t n) {
         case BPLG_OP_FFT_TC: {
             m.bpe = 16;
             if (p.op == BPLG_OP_FFT_TC && p.io == 2) {
-                // two 64-point GEMM passes: per element a split and a store of
-                // each operand, one twiddle, the tensor-memory reads; the next
-                // tile's loads in flight behind the products
-                m.instr = P * 24.0 + 40;
+                // two 64-point GEMM passes in a persistent loop: per element
+                // two splits and operand stores, one twiddle, two
+                // tensor-memory reads with neighbour exchanges (about 60
+                // instructions); the next tile's loads in flight behind the
+                // products
+                m.instr = P * 60.0 + 100;
                 m.bars = 4;
                 m.acc = 2.0 * P;
                 m.lines = 2;
-                m.piped = true;
+                m.persistent = true;
                 break;
             }
             const int r = p.radix, lr = lg2i(r), logn = lg2i(n);
@@ -437,12 +440,16 @@ double model_kernel(const ModelOp &m, const DevModel &dm, int64_t elems, int64_t
     const double t_comp = std::max(wpb * m.instr / kModelIpc, m.instr * kModelCpi) / dm.clk +
                           m.bars * kModelBarrier * (1.0 + wpb / 16.0) / dm.clk;
     const double res = kModelLatency * (m.piped ? 0.5 : 1.0) + t_xfer + t_comp;
+    // a persistent block overlaps a tile's transfer with the previous tile's
+    // work and pays the latency and the launch once
+    const double t_lat = m.persistent ? per_sm_blocks * std::max(t_xfer, t_comp) / b_a + kModelLatency
+                                      : per_sm_blocks * res / b_a;
     const double terms[6] = {
-        per_sm_blocks * res / b_a,                                        // latency, b_a blocks in flight
+        t_lat,                                                            // latency, b_a blocks (tiles) in flight
         static_cast<double>(elems) * m.bpe / dm.bw,                       // HBM bandwidth
         per_sm_blocks * wpb * m.instr / (kModelIpc * dm.clk),             // issue
         per_sm_blocks * wpb * m.acc * m.lines * kModelLine / dm.clk,      // lines through the load/store unit
-        per_sm_blocks * kModelBlockLaunch,                                // block launches
+        (m.persistent ? 1.0 : per_sm_blocks) * kModelBlockLaunch,         // block launches
         static_cast<double>(elems) * m.fp64 / (sms * kModelFp64PerClk * dm.clk)};  // FP64 pipe
     double s = 0.0;
     for (double t : terms) s += std::pow(t, kModelNorm);
@@ -499,8 +506,10 @@ double model_plan_time(const bplg_plan &p, int64_t n, int64_t batch, int regs, i
     }
     const ModelOp m = model_op(p, n);
     const int64_t spb = std::max(1, p.spb);
-    const int64_t blocks = (batch + spb - 1) / spb;
-    return model_kernel(m, dm, n * batch, blocks, p.L, regs, smem, static_cast<int>(spb * n));
+    const int64_t blocks = (batch + spb - 1) / spb;  // tiles of a persistent kernel
+    // the 4096-point two-pass tensor-core kernel adds the warp that issues the products
+    const int threads = p.op == BPLG_OP_FFT_TC && p.io == 2 && n == 4096 ? p.L + 32 : p.L;
+    return model_kernel(m, dm, n * batch, blocks, threads, regs, smem, static_cast<int>(spb * n));
 }
 
 // ------------------------------------------------- Bayesian optimisation
