@@ -1156,8 +1156,9 @@ def largefft_report(args):
 def nonpow2_report(args):
     """Lengths that are not powers of two, 2^24 elements per case: the padded
     scan (int32) and Wang-Mou solve on the next power of two against the
-    power-of-two length just below, and Bluestein FFTs against cuFFT (which
-    runs such lengths with its own mixed-radix or Bluestein kernels).  Every
+    power-of-two length just below, and FFTs against cuFFT (mixed radix for
+    2^a 3^b 5^c up to 12288, Bluestein otherwise; cuFFT runs such lengths
+    with its own mixed-radix or Bluestein kernels).  Every
     row reports the time, Gelem/s and the fraction of the measured copy
     bandwidth for the algorithmic bytes (scan 8, tridiag 20, FFT 16 per
     element)."""
@@ -1207,16 +1208,24 @@ def nonpow2_report(args):
         p = bp.query_plan(bp.OP_TRIDIAG_WM, bp.F32, 1 << (n - 1).bit_length(), batch)
         rows.append(line("tridiag_wm", n, batch, timeit(lambda: bp.tridiag_batched(*ts, xo, n, batch, plan=p)), 20,
                          {"plan_n": p.n}))
-    for n in (1000, 3000, 100003):
+    for n in (1000, 3000, 6000, 10000, 375, 1001, 4095, 100003):
         batch = max(1, total // n)
         z = torch.rand(2 * n * batch, device="cuda") * 2 - 1
         zo = torch.empty_like(z)
         ms = timeit(lambda: bp.fft_batched(z, zo, n, batch, -1))
         tc = timeit(lambda: lib.extref_fft_c2c(ctypes.c_void_p(z.data_ptr()), ctypes.c_void_p(zo.data_ptr()), n, batch,
                                                -1, ctypes.c_void_p(st.cuda_stream)))
-        M = 1 << (2 * n - 2).bit_length()
-        rows.append(line("fft_bluestein", n, batch, ms, 16, {"inner_M": M, "cufft_ms": round(tc, 5),
-                                                             "ours_speedup_vs_cufft": round(tc / ms, 3)}))
+        v = n
+        for f in (2, 3, 5):
+            while v % f == 0:
+                v //= f
+        extra = {"cufft_ms": round(tc, 5), "ours_speedup_vs_cufft": round(tc / ms, 3)}
+        if v == 1 and n <= 12288:
+            kind = "fft_mixed_radix"
+        else:
+            kind = "fft_bluestein"
+            extra["inner_M"] = 1 << (2 * n - 2).bit_length()
+        rows.append(line(kind, n, batch, ms, 16, extra))
     return rows
 
 

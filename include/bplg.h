@@ -179,34 +179,48 @@ int bplg_scan_batched(int32_t dtype, const void *in, void *out, int64_t n, int64
  *          complex values that the library allocates on first use per device
  *          and stream and grows when needed (a growth waits for the stream);
  *          in may equal out.
- *          A length that is not a power of two runs Bluestein's chirp
- *          identity: X_k = h_k sum_j (x_j h_j) conj(h_{k-j}) with
+ *          A length n = 2^a 3^b 5^c up to 12288 that is not a power of two
+ *          (and no plan) runs a mixed-radix Stockham kernel: stages of
+ *          radix 8, 5, 4, 3 and 2, the block's signals in shared memory,
+ *          the stage twiddles from a per-n table W_n^e made on the first
+ *          call with that n (float64 on the host, rounded to float32,
+ *          uploaded synchronously).
+ *          Any other length that is not a power of two runs Bluestein's
+ *          chirp identity: X_k = h_k sum_j (x_j h_j) conj(h_{k-j}) with
  *          h_m = exp(dir pi i m^2 / n), a cyclic convolution of length
- *          M = next power of two >= 2n - 1 computed with two M-point FFTs
- *          (plan: a plan for M, or NULL) and three elementwise kernels,
- *          through a scratch of M * batch complex values per device and
- *          stream.  The chirp and the transformed chirp are per-(n, dir)
- *          tables made on the first call with that n (float64 on the host,
- *          rounded to float32; uploaded synchronously).
+ *          M = next power of two >= 2n - 1.  With no plan and 32 <= M <=
+ *          8192 it is one fused kernel; otherwise (or with a plan, which
+ *          must be made for M) two M-point FFTs and three elementwise
+ *          kernels through a scratch of M * batch complex values per device
+ *          and stream.  The chirp and the transformed chirp are per-(n, dir)
+ *          tables made like the mixed-radix table.
  * Twiddles W_M^k are generated once per device in float64 and rounded to
  * float32.  Errors: INVALID_ARG, UNSUPPORTED_SIZE, INVALID_PLAN, CUDA. */
 int bplg_fft_batched(const void *in, void *out, int64_t n, int64_t batch, int32_t dir,
                      const bplg_plan *plan, void *stream);
 
-/* The same FFT with every radix-16 Stockham stage run on tensor cores: each
- * 16-point DFT of a stage is a 32 x 32 real contraction on 16-bit operands
- * split into hi and lo parts, x = xh + xl and F = Fh + Fl, summing
- * xh Fh + xh Fl + xl Fh in float32.  Plan io 0 (the default) issues the
- * contractions as tcgen05.mma with the accumulator in tensor memory (n >=
- * 1024); io 1 is the legacy mma.sync m16n8k16 form.  Twiddles are applied in
- * float32 from the float64-generated table, and a mixed-radix first stage
- * (log2 n not a multiple of 4) runs on the CUDA cores.  Not in
+/* The same FFT with its DFT stages run on tensor cores as real contractions
+ * on 16-bit operands split into hi and lo parts, x = xh + xl and
+ * F = Fh + Fl, summing xh Fh + xh Fl + xl Fh in float32.
+ *   io 0 (n >= 1024): every radix-16 stage; each 16-point DFT is a 32 x 32
+ *        contraction issued as tcgen05.mma with the accumulator in tensor
+ *        memory; a mixed-radix first stage (log2 n not a multiple of 4)
+ *        runs on the CUDA cores.
+ *   io 1: the same stages in the legacy mma.sync m16n8k16 form.
+ *   io 2 (n = 4096: P 16, spb 2; n = 16384: P 32, spb 1; 512 threads):
+ *        two passes of 64-point DFTs (the 64 x 64 four-step form; 16384
+ *        points after a radix-4 stage on the CUDA cores), each pass one
+ *        chain of K = 128 products with the 128 x 128 DFT matrix held in
+ *        tensor memory, in a persistent kernel that loads the next tile
+ *        while the current one runs.
+ * Twiddles are applied in float32 from the float64-generated table.  Not in
  * the paper (whose FFT is float32 on CUDA cores, Section III); the error
  * against the float64 oracle is reported per size.
  *   precision BPLG_TC_BF16 or BPLG_TC_F16 (FP16 scales each stage by 1/4,
  *             exactly, and undoes it at the end).
  *   n        power of two, 512 <= n <= 16384; in, out as bplg_fft_batched.
- *   plan     op BPLG_OP_FFT_TC (P = radix = 16, spb), or NULL.
+ *   plan     op BPLG_OP_FFT_TC (radix 16; P, spb, io as above), or NULL
+ *            (the GB300 cost model's choice).
  * Errors: INVALID_ARG, UNSUPPORTED_SIZE, INVALID_PLAN, CUDA. */
 int bplg_fft_tc_batched(const void *in, void *out, int64_t n, int64_t batch, int32_t dir,
                         int32_t precision, const bplg_plan *plan, void *stream);

@@ -137,6 +137,8 @@ int bplg_fft_batched(const void *in, void *out, int64_t n, int64_t batch, int32_
     if (n < 1 || batch < 1) return set_error(BPLG_ERR_INVALID_ARG, "fft: n and batch must be >= 1");
     if (dir != -1 && dir != 1) return set_error(BPLG_ERR_INVALID_ARG, "fft: dir must be -1 or +1");
     if (!aligned16(in) || !aligned16(out)) return set_error(BPLG_ERR_INVALID_ARG, "fft: buffers must be 16-byte aligned");
+    if (!is_pow2(n) && !plan && fft_mixed_supported(n))
+        return fft_mixed_launch(in, out, n, batch, dir, static_cast<cudaStream_t>(stream));
     if (!is_pow2(n) && n > 2 && n <= (int64_t(1) << kBluesteinMaxLog))
         return fft_bluestein_launch(plan, in, out, n, batch, dir, static_cast<cudaStream_t>(stream));
     if (!size_ok(BPLG_OP_FFT, n, 2))

@@ -1,6 +1,7 @@
 """Lengths that are not powers of two: the scan and the Wang-Mou tridiagonal
 solver run the plan of the next power of two with identity padding, the FFT
-runs Bluestein's chirp identity over power-of-two FFTs.  Parity against the
+runs a mixed-radix Stockham kernel for 2^a 3^b 5^c up to 12288 and
+Bluestein's chirp identity over power-of-two FFTs otherwise.  Parity against the
 oracle (scan bit-exact for int32, the float64 Thomas solution <= 1e-4, the
 O(N^2) DFT <= 1e-5 ceil(log2 N)), closed forms at sizes the O(N^2) oracle
 cannot reach, every plan of the padded size, and nothing written past n."""
@@ -119,14 +120,75 @@ def run_fft(bp, x, direction, plan=None, guard=16):
     return o[:2 * batch * n].view(np.complex64).reshape(batch, n)
 
 
-@pytest.mark.parametrize("n", [3, 5, 6, 7, 12, 100, 243, 1000, 1536, 3000])
+# lengths with a prime factor above 5: Bluestein (fused kernel for M = 32 ..
+# 8192, i.e. n = 17 .. 4096; three launches below and above)
+@pytest.mark.parametrize("n", [7, 14, 77, 1001, 4095])
 def test_fft_bluestein_vs_dft(bp, n):
-    batch = 6 if n <= 1000 else 2
+    batch = 6 if n <= 1001 else 2
     x = si.fft_c64(batch, n, stream=800 + n)
     for direction in (-1, 1):
         X = run_fft(bp, x, direction)
         ref = oracle.dft(x, direction)
         assert fft_rel_err(X, ref).max() <= tol(n), (n, direction)
+
+
+# 2^a 3^b 5^c (not a power of two, at most 12288): the mixed-radix Stockham
+# kernel, radices 16, 8, 5, 4, 3, 2; odd lengths take the 8-byte load path,
+# small ones several signals a block (ragged last block)
+@pytest.mark.parametrize("n", [3, 5, 6, 9, 10, 12, 15, 20, 25, 27, 45, 60, 81, 100, 120, 125, 243, 360, 375, 625,
+                               1000, 1215, 1536, 2187, 3000])
+def test_fft_mixed_radix_vs_dft(bp, n):
+    batch = 37 if n <= 100 else (5 if n < 1000 else 1)
+    x = si.fft_c64(batch, n, stream=1800 + n)
+    for direction in (-1, 1):
+        X = run_fft(bp, x, direction)
+        ref = oracle.dft(x, direction)
+        assert fft_rel_err(X, ref).max() <= tol(n), (n, direction)
+
+
+@pytest.mark.parametrize("n", [3125, 6000, 10000, 12288])
+def test_fft_mixed_radix_large_closed_forms(bp, n):
+    """Beyond the O(N^2) oracle's reach: an impulse at j0 gives exp(-2 pi i
+    j0 k / n), a tone at f gives n at bin f (both directions), and a random
+    signal survives the forward-inverse round trip."""
+    k = np.arange(n, dtype=np.float64)
+    j0, f = 1234 % n, 777 % n
+    for direction in (-1, 1):
+        imp = np.zeros((3, n), np.complex64)
+        imp[:, j0] = 1
+        X = run_fft(bp, imp, direction).astype(np.complex128)
+        ref = np.exp(direction * 2j * np.pi * ((j0 * k) % n) / n)
+        assert fft_rel_err(X, np.broadcast_to(ref, X.shape)).max() <= tol(n)
+        tone = np.exp(-direction * 2j * np.pi * ((f * k) % n) / n).astype(np.complex64)[None, :]
+        Y = run_fft(bp, tone, direction)[0].astype(np.complex128)
+        spike = np.zeros(n, np.complex128)
+        spike[f] = n
+        assert np.linalg.norm(Y - spike) / np.linalg.norm(spike) <= tol(n)
+    x = si.fft_c64(3, n, stream=2200 + n)
+    y = run_fft(bp, run_fft(bp, x, -1), +1).astype(np.complex128) / n
+    assert fft_rel_err(y, x.astype(np.complex128)).max() <= 2 * tol(n)
+
+
+def test_fft_mixed_radix_large_batch_sampled(bp):
+    """A full-size batch (2^24 elements of n = 1000) checked on sampled signals."""
+    n = 1000
+    batch = (1 << 24) // n
+    x = si.fft_c64(batch, n, stream=1999)
+    X = run_fft(bp, x, -1)
+    rows = np.unique(np.random.default_rng(4).integers(0, batch, 24))
+    assert fft_rel_err(X[rows], oracle.dft(x[rows], -1)).max() <= tol(n)
+
+
+@pytest.mark.parametrize("n", [375, 3000])
+def test_fft_mixed_radix_round_trip_in_place(bp, n):
+    batch = 5
+    x = si.fft_c64(batch, n, stream=2100 + n)
+    t = c64_to_dev(x.reshape(-1))
+    bp.fft_batched(t, t, n, batch, -1)
+    bp.fft_batched(t, t, n, batch, +1)
+    torch.cuda.synchronize()
+    y = c64_from_dev(t).reshape(batch, n) / n
+    assert fft_rel_err(y, x.astype(np.complex128)).max() <= 2 * tol(n)
 
 
 def test_fft_bluestein_round_trip_and_in_place(bp):
