@@ -76,13 +76,15 @@ def read_peaks():
 # batch, doubled; keyed by row and plan.  A launch whose plan was not captured
 # reports null.
 NCU_TRAFFIC = {
-    # tridiag_refined_reg_kernel, layout 6, P = 16: DRAM read + write of one
-    # half-size launch, doubled (the rest of x is still in L2 at kernel end)
+    # DRAM read + write of one half-size launch of the kernel as it stands,
+    # doubled (the rest of x is still in L2 at kernel end).  Layout 6, P = 16:
+    # tridiag_refined_reg_kernel
     ("refined_1024", (("P", 16), ("L", 64), ("spb", 1), ("shuffle", 1), ("pattern", 0), ("smem_layout", 6),
                       ("smem_pad", 0), ("io", 0), ("cr_switch", 32))): 2 * (134331648 + 26756608),
-    # the Wang-Mou layout (7), P = 8: tridiag_refined_reg_kernel_mb (72 registers)
+    # the Wang-Mou layout (7), P = 8: tridiag_refined_reg_kernel_mb<..., 7> (72
+    # registers, seven threads-per-system bits at compile time)
     ("refined_1024", (("P", 8), ("L", 128), ("spb", 1), ("shuffle", 1), ("pattern", 0), ("smem_layout", 7),
-                      ("smem_pad", 0), ("io", 0), ("cr_switch", 32))): 2 * (134292992 + 27802368),
+                      ("smem_pad", 0), ("io", 0), ("cr_switch", 32))): 2 * (134336768 + 28204288),
 }
 
 # FP64 issue rate of one SM: 2 double-precision fused multiply-adds per clock
@@ -1281,6 +1283,42 @@ def precision_report(args):
     return out
 
 
+def case_run(args):
+    """One FFT case on its own, for profiling: `--case fft` (bplg_fft_batched:
+    any n, power of two, mixed radix or Bluestein) or `--case fft_tc`
+    (bplg_fft_tc_batched with the first enumerated plan of `--io`, split
+    `--precision`), forward, on 2^24 / n signals (or `--batch`) of U[-1, 1]
+    data: `--warmup` untimed calls, then `--steps` timed ones; prints one
+    JSON line with the mean time."""
+    import torch
+    torch.cuda.set_device(0)
+    import paper_2310_16214_gb300 as bp
+    n = args.n
+    batch = args.batch or max(1, (1 << 24) // n)
+    g = torch.Generator(device="cuda").manual_seed(args.seed)
+    z = torch.rand(2 * n * batch, device="cuda", generator=g) * 2 - 1
+    o = torch.empty_like(z)
+    if args.case == "fft_tc":
+        plan = [q for q in bp.enumerate_plans(bp.OP_FFT_TC, bp.F32, n) if q.io == args.io][0]
+        fn = lambda: bp.fft_tc_batched(z, o, n, batch, -1, args.precision, plan=plan)
+    else:
+        plan = None
+        fn = lambda: bp.fft_batched(z, o, n, batch, -1)
+    for _ in range(args.warmup):
+        fn()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        fn()
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / max(1, args.steps)
+    print(json.dumps({"case": args.case, "n": n, "batch": batch, "ms": round(ms, 5),
+                      "hbm_frac": round(16 * n * batch / (ms * 1e-3) / 1e9 / read_peaks()[0], 4),
+                      "plan": plan.as_dict() if plan is not None else None, "device_status": bp.device_status()}))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -1305,6 +1343,12 @@ def main():
                     help="FFTs above 16384 points: tuners vs exhaustive (Phi) and cuFFT")
     ap.add_argument("--uneven-report", action="store_true",
                     help="the uneven batch's graph launch against one tuned batched launch per size class")
+    ap.add_argument("--case", default="", choices=["", "fft", "fft_tc"],
+                    help="time one FFT case (--n, --batch, --io, --precision) instead of the bench")
+    ap.add_argument("--n", type=int, default=4096)
+    ap.add_argument("--batch", type=int, default=0)
+    ap.add_argument("--io", type=int, default=2)
+    ap.add_argument("--precision", type=int, default=1, help="tensor-core split: 0 BF16, 1 FP16")
     ap.add_argument("--ops", default="", help="comma-separated ops for --tune-report")
     ap.add_argument("--reps", type=int, default=50)
     ap.add_argument("--bo-budget", type=int, default=40)
@@ -1323,6 +1367,8 @@ def main():
         uneven_report(args)
     elif args.nonpow2_report:
         nonpow2_report(args)
+    elif args.case:
+        case_run(args)
     elif args.largefft_report:
         largefft_report(args)
     elif args.impl == "reference":
