@@ -510,7 +510,9 @@ def run_ours(args):
     roofline = dominant_roofline(dom, per_item[dom["name"]], peak, peak_kind, refined_iters, clocks, fp64_peak)
     step_ms = total_ms / args.steps
     value = job_value(world, wl.elems, step_ms)
-    launches_per_step = len(wl.items)
+    # kernels launched per step: one per row, three for the uneven batch's
+    # graph (one persistent kernel per operation)
+    launches_per_step = sum(3 if it["op"] == "uneven" else 1 for it in wl.items)
     items_out = {it["name"]: {"ms": round(per_item[it["name"]], 5),
                               "median_ms": round(per_item_median[it["name"]], 5),
                               "p10_ms": round(per_item_pct[it["name"]][0], 5),
