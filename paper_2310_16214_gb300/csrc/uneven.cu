@@ -113,18 +113,21 @@ __global__ void __launch_bounds__(kUnevenScanThreads)
     __shared__ int s_unit;
     __shared__ int32_t tot_i[32];
     __shared__ float tot_f[32];
+    if (threadIdx.x == 0) s_unit = atomicAdd(counter, 1);
+    __syncthreads();
     for (;;) {
-        if (threadIdx.x == 0) s_unit = atomicAdd(counter, 1);
-        __syncthreads();
         const int u = s_unit;
-        __syncthreads();  // every thread has read s_unit before it is rewritten
         if (u >= nunits) break;
+        int next = 0;
+        if (threadIdx.x == 0) next = atomicAdd(counter, 1);  // the next unit, fetched while this one runs
         const UnitDesc U = units[u];
         if (U.flags == BPLG_I32)
             scan_unit_dispatch<int32_t>(items, U, tot_i);
         else
             scan_unit_dispatch<float>(items, U, tot_f);
-        __syncthreads();  // warp totals are reused by the next unit
+        __syncthreads();  // warp totals are reused by the next unit; every thread has read s_unit
+        if (threadIdx.x == 0) s_unit = next;
+        __syncthreads();
     }
 }
 
@@ -173,18 +176,21 @@ __global__ void __launch_bounds__(kUnevenFftThreads, 2)
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ int s_unit;
     float2 *buf = reinterpret_cast<float2 *>(smem_raw);
+    if (threadIdx.x == 0) s_unit = atomicAdd(counter, 1);
+    __syncthreads();
     for (;;) {
-        if (threadIdx.x == 0) s_unit = atomicAdd(counter, 1);
-        __syncthreads();
         const int u = s_unit;
-        __syncthreads();
         if (u >= nunits) break;
+        int next = 0;
+        if (threadIdx.x == 0) next = atomicAdd(counter, 1);  // the next unit, fetched while this one runs
         const UnitDesc U = units[u];
         if (U.flags < 0)
             fft_unit_any<-1>(items, U, tw, buf);
         else
             fft_unit_any<1>(items, U, tw, buf);
-        __syncthreads();  // the exchange buffer is reused by the next unit
+        __syncthreads();  // the exchange buffer is reused by the next unit; every thread has read s_unit
+        if (threadIdx.x == 0) s_unit = next;
+        __syncthreads();
     }
 }
 
@@ -221,15 +227,18 @@ __global__ void __launch_bounds__(kUnevenTriThreads, 2)
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ int s_unit;
     float4 *smem = reinterpret_cast<float4 *>(smem_raw);
+    if (threadIdx.x == 0) s_unit = atomicAdd(counter, 1);
+    __syncthreads();
     for (;;) {
-        if (threadIdx.x == 0) s_unit = atomicAdd(counter, 1);
-        __syncthreads();
         const int u = s_unit;
-        __syncthreads();
         if (u >= nunits) break;
+        int next = 0;
+        if (threadIdx.x == 0) next = atomicAdd(counter, 1);  // the next unit, fetched while this one runs
         const UnitDesc U = units[u];
         tri_unit<kUnevenTriP>(items, U, smem);
-        __syncthreads();  // the exchange buffers are reused by the next unit
+        __syncthreads();  // the exchange buffers are reused by the next unit; every thread has read s_unit
+        if (threadIdx.x == 0) s_unit = next;
+        __syncthreads();
     }
 }
 
