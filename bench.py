@@ -1099,9 +1099,10 @@ def uneven_report(args):
 
 def largefft_report(args):
     """FFTs above 16384 points (two kernels), N in {2^16, 2^18, 2^20, 2^22},
-    2^24 / N signals: the analytical, learned and exhaustive plans over the
-    joint knob space (split N1, columns per block, rows per block), each
-    re-timed, Phi for both tuners, and cuFFT on the same workload.  The
+    2^24 / N signals: the GB300 cost model's, the analytical guideline's,
+    the learned and the exhaustive plans over the joint knob space (split
+    N1, columns per block, rows per block), each re-timed, Phi for the three
+    tuners, and cuFFT on the same workload.  The
     algorithmic bytes are 16 per element, though the two passes move 32."""
     import ctypes
     import torch
@@ -1126,21 +1127,23 @@ def largefft_report(args):
         torch.cuda.synchronize()
         return statistics.median(a.elapsed_time(b) for a, b in evs)
 
-    rows, e_an, e_le = [], [], []
+    rows, e_an, e_le, e_mo = [], [], [], []
     for logn in (16, 18, 20, 22):
         n = 1 << logn
         batch = (1 << 24) // n
         zin = torch.rand(2 * n * batch, device="cuda") * 2 - 1
         zout = torch.empty_like(zin)
         pa, _ = bp.tune_plan(bp.OP_FFT, bp.F32, n, batch, bp.TUNE_ANALYTIC)
+        pm, _ = bp.tune_plan(bp.OP_FFT, bp.F32, n, batch, bp.TUNE_MODEL)
         pl, rl = bp.tune_plan(bp.OP_FFT, bp.F32, n, batch, bp.TUNE_LEARNED, budget=args.bo_budget, seed=args.seed)
         pe, re_ = bp.tune_plan(bp.OP_FFT, bp.F32, n, batch, bp.TUNE_EXHAUSTIVE)
         t = {k: timeit(lambda p=p: bp.fft_batched(zin, zout, n, batch, -1, plan=p))
-             for k, p in (("analytic", pa), ("learned", pl), ("exhaustive", pe))}
+             for k, p in (("model", pm), ("analytic", pa), ("learned", pl), ("exhaustive", pe))}
         best = min(t.values())
         tc = timeit(lambda: lib.extref_fft_c2c(ctypes.c_void_p(zin.data_ptr()), ctypes.c_void_p(zout.data_ptr()), n,
                                                batch, -1, ctypes.c_void_p(st.cuda_stream)))
         e_an.append(best / t["analytic"])
+        e_mo.append(best / t["model"])
         e_le.append(best / t["learned"])
         row = {"n": n, "batch": batch, "space": re_.space_size, "bo_evaluations": rl.evaluations,
                "ms": {k: round(v, 5) for k, v in t.items()},
@@ -1149,11 +1152,12 @@ def largefft_report(args):
                "hbm_frac_two_pass": round(32 * n * batch / (best * 1e-3) / 1e9 / peak, 4),
                "cufft_ms": round(tc, 5), "ours_speedup_vs_cufft": round(tc / best, 3),
                "plans": {k: {"n1_log": p.n1_log, "spb": p.spb, "row_spb": p.row_spb}
-                         for k, p in (("analytic", pa), ("learned", pl), ("exhaustive", pe))}}
+                         for k, p in (("model", pm), ("analytic", pa), ("learned", pl), ("exhaustive", pe))}}
         rows.append(row)
         print(json.dumps(row), flush=True)
     phi = lambda es: round(len(es) / sum(1.0 / e for e in es), 4)
-    print(json.dumps({"largefft_report": {"phi_analytic": phi(e_an), "phi_learned": phi(e_le)}}), flush=True)
+    print(json.dumps({"largefft_report": {"phi_model": phi(e_mo), "phi_analytic": phi(e_an), "phi_learned": phi(e_le)}}),
+          flush=True)
     return rows
 
 

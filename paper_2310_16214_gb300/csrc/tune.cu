@@ -487,7 +487,11 @@ double model_plan_time(const bplg_plan &p, int64_t n, int64_t batch, int regs, i
     if (p.op == BPLG_OP_FFT && n > (int64_t(1) << kFftMaxLog) && p.n1_log > 0) {
         const int l1 = p.n1_log, l2 = lg2i(n) - p.n1_log;
         const int64_t n1 = int64_t(1) << l1, n2 = int64_t(1) << l2;
-        auto pass = [&](int64_t len, int per_block, int64_t cnt, int rg, int sm, double lines) {
+        // a pass whose HBM accesses are segments of `seg` contiguous bytes
+        // (rows far apart) pays for partial lines: sqrt(128 / seg) per byte
+        // below a whole 128-byte line (32 bytes cost twice as much)
+        auto seg_cost = [](double seg) { return std::sqrt(std::max(1.0, 128.0 / seg)); };
+        auto pass = [&](int64_t len, int per_block, int64_t cnt, int rg, int sm, double lines, double bytes_factor) {
             bplg_plan q = p;
             q.radix = q.P = 16;
             q.io = 0;
@@ -496,12 +500,17 @@ double model_plan_time(const bplg_plan &p, int64_t n, int64_t batch, int regs, i
             ModelOp m = model_op(q, len);
             m.instr += 16 * 4.0;  // the large-transform twiddle or the transposed store
             m.lines = lines;
+            m.bpe *= bytes_factor;
             const int threads = static_cast<int>(per_block * (len / 16));
             return model_kernel(m, dm, n * batch, batch * cnt, threads, rg, sm, static_cast<int>(per_block * len));
         };
-        const double c = pass(n1, p.spb, n2 / std::max(1, p.spb), regs, smem, grouped_lines(p.spb, 8.0));
+        // columns: loads and stores in segments of spb values; rows: loads
+        // whole rows, stores transposed in segments of row_spb values
+        const double c = pass(n1, p.spb, n2 / std::max(1, p.spb), regs, smem, grouped_lines(p.spb, 8.0),
+                              seg_cost(8.0 * p.spb));
         const double r = pass(n2, p.row_spb, n1 / std::max(1, p.row_spb), regs2 > 0 ? regs2 : regs,
-                              smem2 > 0 ? smem2 : smem, grouped_lines(p.row_spb, 8.0));
+                              smem2 > 0 ? smem2 : smem, grouped_lines(p.row_spb, 8.0),
+                              0.5 * (1.0 + seg_cost(8.0 * p.row_spb)));
         return c + r;
     }
     const ModelOp m = model_op(p, n);
