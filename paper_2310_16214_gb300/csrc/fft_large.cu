@@ -57,7 +57,12 @@ __device__ __forceinline__ float2 twiddle_n(const float2 *__restrict__ tw, const
 }
 
 __host__ __device__ constexpr int col_stride(int n1) { return n1 + n1 / 16 + 1; }  // float2, skewed
-__host__ __device__ constexpr int row_stride(int n2) { return n2 + n2 / 16 + 1; }
+// rows of the row kernel: a pad of 16 / R float2 (R = rows per block <= 16)
+// puts the R rows of the transposed read-out 32 / R banks apart, so the 16
+// lanes of each half-warp (16 / R columns x R rows) hit 16 bank pairs
+__host__ __device__ constexpr int row_stride(int n2, int log_rows) {
+    return n2 + n2 / 16 + (log_rows <= 4 ? (16 >> log_rows) : 1);
+}
 
 template <int LOGN1, int DIR>
 __global__ void __launch_bounds__(1024)
@@ -92,7 +97,7 @@ __global__ void __launch_bounds__(1024)
     fft_row_kernel(const float2 *y, float2 *out, const float2 *__restrict__ tw, int logn, int log_rows) {
     using S = FftShape<16, LOGN2>;
     constexpr int N2 = 1 << LOGN2;
-    constexpr int RS = row_stride(N2);
+    const int RS = row_stride(N2, log_rows);
     extern __shared__ __align__(16) unsigned char smem_raw[];
     float2 *rows = reinterpret_cast<float2 *>(smem_raw);
     const int logn1 = logn - LOGN2;
@@ -238,7 +243,7 @@ bool pow2_in(int v, int lo, int hi) { return v >= lo && v <= hi && (v & (v - 1))
 int fft_large_smem_bytes(const bplg_plan &p, int64_t n, int pass) {
     const int l1 = p.n1_log, l2 = ilog2(n) - p.n1_log;
     if (pass == 0) return p.spb * col_stride(1 << l1) * 8;
-    return p.row_spb * row_stride(1 << l2) * 8;
+    return p.row_spb * row_stride(1 << l2, ilog2(p.row_spb)) * 8;
 }
 
 bool fft_large_plan_valid(const bplg_plan &p, int64_t n, std::string *why) {
