@@ -361,7 +361,11 @@ ModelOp model_op(const bplg_plan &p, int64_t n) {
             double stage = bf + 3.0 + idx;                                       // + twiddle
             if (p.op == BPLG_OP_FFT_TC) stage += p.io == 0 ? 6.0 : 30.0;          // hi/lo split, MMA round trip
             m.instr = r * (K * stage + xch) + 12;
-            m.bars = 2.0 * (K - 1) + (p.op == BPLG_OP_FFT_TC ? 2.0 * K : 0.0);
+            // tensor-core stages: io 0 waits each stage for its tcgen05
+            // products (write A, barrier, issue, commit, mbarrier wait,
+            // tensor-memory read: two hand-offs, about 1 us a stage, 32
+            // barriers' worth); io 1 gathers fragments
+            m.bars = 2.0 * (K - 1) + (p.op == BPLG_OP_FFT_TC ? (p.io == 0 ? 32.0 : 2.0) * K : 0.0);
             if (p.io == 1) {
                 m.instr += r * 4;
                 m.bars += 2;

@@ -113,3 +113,23 @@ def test_two_gemm_pass_kernel_in_place(bp, n):
     bp.fft_tc_batched(buf, buf, n, batch, -1, precision=1, plan=plan)
     torch.cuda.synchronize()
     assert fft_rel_err(c64_from_dev(buf), oracle.fft(z, -1)).max() <= 1e-5 * math.log2(n)
+
+
+@pytest.mark.parametrize("n", [4096, 16384])
+def test_two_gemm_pass_kernel_at_the_precision_configuration(bp, n):
+    """io 2 at the precision configuration's full size (2^26 / N signals),
+    both splits and directions, checked on sampled signals; it is also the
+    cost model's default tensor-core plan at these sizes (measured faster
+    than the radix-16 stages there)."""
+    plan = _gemm_plan(bp, n)
+    batch = (1 << 26) // n
+    z = si.fft_c64(batch, n, seed=si.CONFIG_SEEDS["precision"], stream=n)
+    rows = np.unique(np.concatenate([sample_rows(batch, k=16), [0, batch - 1]]))
+    for d in (-1, 1):
+        ref = oracle.fft(z[rows], d)
+        for prec in (0, 1):
+            X = run(bp, z, d, prec, plan)
+            err = fft_rel_err(X[rows], ref).max()
+            assert err <= 1e-5 * math.log2(n), (d, prec, err)
+    assert bp.device_status() == 0
+    assert bp.query_plan(bp.OP_FFT_TC, bp.F32, n, batch).io == 2
