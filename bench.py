@@ -153,6 +153,9 @@ def dominant_roofline(dom, dom_ms, peak, peak_kind, refined_iters, clocks, fp64_
         return {"bound": "alu", "pipe": "fp64", "kernel": dom["name"], "achieved": round(achieved, 4),
                 "peak": round(fp64, 4), "peak_kind": kind, "derived_peak": round(derived, 4),
                 "unit": "TFLOP/s", "frac": round(achieved / fp64, 4), "traffic": traffic,
+                "traffic_note": ("DRAM read + write of one ncu capture of this kernel and plan on the half-size "
+                                 "case, doubled; part of x was still in L2 when that kernel ended, so the write "
+                                 "side is below the algorithmic 8 B per unknown") if traffic else None,
                 "algorithmic_flops": flops, "algorithmic_bytes": dom["bytes"], "launch_ms": round(dom_ms, 5),
                 "hbm": {"achieved": round(gbs, 1), "peak": peak, "peak_kind": peak_kind, "frac": round(gbs / peak, 4)}}
     return {"bound": "hbm", "kernel": dom["name"], "achieved": round(gbs, 1), "peak": peak,
