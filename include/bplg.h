@@ -276,7 +276,10 @@ int bplg_fft_batched_noalloc(const void *in, void *out, int64_t n, int64_t batch
  *           c[s][n-1] is taken as 0, rows stay n apart and nothing past n is
  *           read or written (element-wise accesses).
  * No pivoting: the systems must be safe for elimination without pivoting
- * (e.g. strictly diagonally dominant).  Errors: as for the scan. */
+ * (e.g. strictly diagonally dominant).  Pivots are inverted with the fast
+ * float32 reciprocal (__fdividef(1, x)), which gives 0 for |x| > 2^126, so
+ * every pivot's magnitude must stay below 2^126 (systems scaled by 2^100
+ * and 2^-100 are tested).  Errors: as for the scan. */
 int bplg_tridiag_batched(const float *a, const float *b, const float *c, const float *d, float *x,
                          int64_t n, int64_t batch, const bplg_plan *plan, void *stream);
 
