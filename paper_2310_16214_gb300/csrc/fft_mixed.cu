@@ -1,8 +1,8 @@
 // Mixed-radix Stockham FFT for lengths n = 2^a 3^b 5^c that are not powers
-// of two (radices 8, 5, 4, 3, 2), the whole signal in shared memory.
-// (The paper keeps to N = r^n; this extends the radix-r Stockham
-// formulation of Section III to products of small radices, so such lengths
-// need not go through Bluestein's identity.)
+// of two, the whole signal in shared memory.  (The paper keeps to N = r^n;
+// this extends the radix-r Stockham formulation of Section III to products
+// of small radices, so such lengths need not go through Bluestein's
+// identity.)
 //
 // Stockham autosort, decimation in time.  With n = r_1 r_2 ... r_K, after
 // the stages r_1 .. r_{s-1} the array holds, for L = r_1 ... r_{s-1} and
@@ -17,9 +17,15 @@
 // an entry of one n-point table, computed on the host in float64 and
 // rounded to float32, like the power-of-two tables.
 //
-// Blocks hold nsig consecutive signals (nsig n >= 512 where n is small), in
-// two shared-memory buffers that the stages alternate between; the signals
-// are loaded and stored contiguously (16-byte accesses when n is even).
+// Radices 16, 15, 12, 10, 9, 8, 6, 5, 4, 3, 2: the 3- and 5-point DFTs
+// written out, the composite ones as two factors with their inner
+// twiddles computed at compile time (float64 series, rounded once).  The
+// factorisation takes the fewest stages; the block shape and the choice
+// among such factorisations follow mixed_factor below.  Blocks hold nsig
+// consecutive signals in two shared-memory buffers that the stages
+// alternate between; the first stage reads global memory and the last
+// writes it.
+#include <algorithm>
 #include <cmath>
 #include <map>
 #include <mutex>
@@ -36,15 +42,65 @@ namespace {
 constexpr int kMixedMaxStages = 20;
 constexpr int kMixedMaxThreads = 512;
 
-// the stage radices, 3 bits a stage (radix_of_code), first stage lowest
+// The stage radices, 4 bits a stage (an index into kRadices), first stage
+// lowest; threads per signal (every stage's butterfly count is a multiple
+// of it) and signals per block.
+constexpr int kNumRadices = 11;
+constexpr int kRadices[kNumRadices] = {16, 15, 12, 10, 9, 8, 6, 5, 4, 3, 2};
 struct MixedPlan {
     int nst;
     uint64_t codes;
     int r[kMixedMaxStages];  // host side
+    int nsig, threads;
 };
 __host__ __device__ __forceinline__ int radix_of_code(uint64_t codes, int s) {
-    const int c = static_cast<int>((codes >> (3 * s)) & 7u);
-    return c == 0 ? 2 : c == 1 ? 3 : c == 2 ? 4 : c == 3 ? 5 : 8;
+    switch (static_cast<int>((codes >> (4 * s)) & 15u)) {
+        case 0: return 16;
+        case 1: return 15;
+        case 2: return 12;
+        case 3: return 10;
+        case 4: return 9;
+        case 5: return 8;
+        case 6: return 6;
+        case 7: return 5;
+        case 8: return 4;
+        case 9: return 3;
+        default: return 2;
+    }
+}
+
+// cos and sin of 2 pi k / m at compile time, in double: the angle is
+// reduced exactly (by the quadrant of 4k / m) to [0, pi / 2) and the
+// Taylor series of sine and cosine summed there (24 terms: the remainder is
+// below 1e-40 for arguments up to pi / 2)
+constexpr double kPiD = 3.14159265358979323846264338327950288;
+constexpr double taylor_sin(double x) {
+    double t = x, sum = x;
+    for (int i = 1; i < 24; ++i) {
+        t *= -x * x / ((2.0 * i) * (2.0 * i + 1.0));
+        sum += t;
+    }
+    return sum;
+}
+constexpr double taylor_cos(double x) {
+    double t = 1.0, sum = 1.0;
+    for (int i = 1; i < 24; ++i) {
+        t *= -x * x / ((2.0 * i - 1.0) * (2.0 * i));
+        sum += t;
+    }
+    return sum;
+}
+constexpr double cos_2pi(int k, int m) {
+    const int kk = ((k % m) + m) % m;
+    const int q = (4 * kk) / m, r = 4 * kk - q * m;  // angle = (q + r / m) pi / 2
+    const double x = 0.5 * kPiD * r / m;
+    return q == 0 ? taylor_cos(x) : q == 1 ? -taylor_sin(x) : q == 2 ? -taylor_cos(x) : taylor_sin(x);
+}
+constexpr double sin_2pi(int k, int m) {
+    const int kk = ((k % m) + m) % m;
+    const int q = (4 * kk) / m, r = 4 * kk - q * m;
+    const double x = 0.5 * kPiD * r / m;
+    return q == 0 ? taylor_sin(x) : q == 1 ? taylor_cos(x) : q == 2 ? -taylor_sin(x) : -taylor_cos(x);
 }
 
 // In-register 3- and 5-point DFTs, y_q = sum_p v_p exp(DIR 2 pi i p q / R).
@@ -80,11 +136,58 @@ __device__ __forceinline__ void dft5(float2 (&v)[5]) {
 }
 
 template <int R, int DIR>
+__device__ __forceinline__ void dft_any(float2 (&v)[R]);
+
+// R = A B points as A B-point DFTs, twiddles W_R^(n1 k2), then B A-point
+// DFTs (the two-factor Cooley-Tukey step): with n = n1 + A n2 and
+// k = k2 + B k1, X[k] = sum_n1 W_A^(n1 k1) [W_R^(n1 k2) sum_n2 x[n] W_B^(n2 k2)]
+template <int A, int B, int DIR>
+__device__ __forceinline__ void dft_two_factor(float2 (&v)[A * B]) {
+    float2 y[A][B];
+#pragma unroll
+    for (int n1 = 0; n1 < A; ++n1) {
+        float2 u[B];
+#pragma unroll
+        for (int n2 = 0; n2 < B; ++n2) u[n2] = v[n1 + A * n2];
+        dft_any<B, DIR>(u);
+#pragma unroll
+        for (int k2 = 0; k2 < B; ++k2) {
+            if (n1 == 0 || k2 == 0) {
+                y[n1][k2] = u[k2];
+            } else {
+                const float c = static_cast<float>(cos_2pi(n1 * k2, A * B));
+                const float sn = static_cast<float>(DIR * sin_2pi(n1 * k2, A * B));
+                y[n1][k2] = make_float2(u[k2].x * c - u[k2].y * sn, u[k2].x * sn + u[k2].y * c);
+            }
+        }
+    }
+#pragma unroll
+    for (int k2 = 0; k2 < B; ++k2) {
+        float2 w[A];
+#pragma unroll
+        for (int n1 = 0; n1 < A; ++n1) w[n1] = y[n1][k2];
+        dft_any<A, DIR>(w);
+#pragma unroll
+        for (int k1 = 0; k1 < A; ++k1) v[k2 + B * k1] = w[k1];
+    }
+}
+
+template <int R, int DIR>
 __device__ __forceinline__ void dft_any(float2 (&v)[R]) {
     if constexpr (R == 3) {
         dft3<DIR>(v);
     } else if constexpr (R == 5) {
         dft5<DIR>(v);
+    } else if constexpr (R == 6) {
+        dft_two_factor<2, 3, DIR>(v);
+    } else if constexpr (R == 9) {
+        dft_two_factor<3, 3, DIR>(v);
+    } else if constexpr (R == 10) {
+        dft_two_factor<2, 5, DIR>(v);
+    } else if constexpr (R == 12) {
+        dft_two_factor<4, 3, DIR>(v);
+    } else if constexpr (R == 15) {
+        dft_two_factor<3, 5, DIR>(v);
     } else {
         dft_codelet<R, DIR>(v);
     }
@@ -159,7 +262,13 @@ __device__ __forceinline__ void mixed_stage_r(int r, const float2 *src, float2 *
         case 3: mixed_stage<3, DIR, FIRST, LAST>(src, dst, tw, n, c, nsig, nvalid); break;
         case 4: mixed_stage<4, DIR, FIRST, LAST>(src, dst, tw, n, c, nsig, nvalid); break;
         case 5: mixed_stage<5, DIR, FIRST, LAST>(src, dst, tw, n, c, nsig, nvalid); break;
-        default: mixed_stage<8, DIR, FIRST, LAST>(src, dst, tw, n, c, nsig, nvalid); break;
+        case 6: mixed_stage<6, DIR, FIRST, LAST>(src, dst, tw, n, c, nsig, nvalid); break;
+        case 8: mixed_stage<8, DIR, FIRST, LAST>(src, dst, tw, n, c, nsig, nvalid); break;
+        case 9: mixed_stage<9, DIR, FIRST, LAST>(src, dst, tw, n, c, nsig, nvalid); break;
+        case 10: mixed_stage<10, DIR, FIRST, LAST>(src, dst, tw, n, c, nsig, nvalid); break;
+        case 12: mixed_stage<12, DIR, FIRST, LAST>(src, dst, tw, n, c, nsig, nvalid); break;
+        case 15: mixed_stage<15, DIR, FIRST, LAST>(src, dst, tw, n, c, nsig, nvalid); break;
+        default: mixed_stage<16, DIR, FIRST, LAST>(src, dst, tw, n, c, nsig, nvalid); break;
     }
 }
 
@@ -167,7 +276,7 @@ __device__ __forceinline__ void mixed_stage_r(int r, const float2 *src, float2 *
 // writes them back; the stages between alternate between two shared-memory
 // buffers.
 template <int DIR>
-__global__ void __launch_bounds__(kMixedMaxThreads, 4)
+__global__ void __launch_bounds__(kMixedMaxThreads, 2)
     fft_mixed_kernel(const float2 *__restrict__ in, float2 *__restrict__ out, const float2 *__restrict__ tw,
                      int nst, uint64_t codes, int n, int nsig, int64_t batch) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -210,27 +319,75 @@ __global__ void __launch_bounds__(kMixedMaxThreads, 4)
     mixed_stage_r<DIR, false, true>(sr[last], (last & 1) ? buf0 : buf1, gout, tw, n, sc[last], nsig, nvalid);
 }
 
-// the stage radices of n, largest first; false unless n = 2^a 3^b 5^c
+// The stage radices of n (false unless n = 2^a 3^b 5^c) and the block
+// shape.  Blocks hold nsig signals (several below 512 points, within 24 KB
+// of shared memory) and T threads, T = the largest stage's butterfly count
+// rounded up to whole warps (at most kMixedMaxThreads), so no stage waits on
+// a second pass of a few threads when one pass could do; among the
+// factorisations with the fewest stages the one with the fewest passes
+// (sum over stages of ceil(butterflies / T)) is taken, then the one with
+// the largest smallest radix.
+void mixed_search(int64_t left, int depth, int *cur, int *best_len, std::vector<std::vector<int>> *found) {
+    if (left == 1) {
+        if (depth < *best_len) {
+            *best_len = depth;
+            found->clear();
+        }
+        if (depth == *best_len) found->push_back(std::vector<int>(cur, cur + depth));
+        return;
+    }
+    if (depth + 1 > *best_len || depth >= kMixedMaxStages) return;
+    for (int i = 0; i < kNumRadices; ++i) {
+        const int r = kRadices[i];
+        if (left % r) continue;
+        if (depth > 0 && r > cur[depth - 1]) continue;  // non-increasing: each multiset once
+        cur[depth] = r;
+        mixed_search(left / r, depth + 1, cur, best_len, found);
+    }
+}
+
 bool mixed_factor(int64_t n, MixedPlan *mp) {
     int64_t v = n;
-    int a = 0, b = 0, c = 0;
-    while (v % 2 == 0) v /= 2, ++a;
-    while (v % 3 == 0) v /= 3, ++b;
-    while (v % 5 == 0) v /= 5, ++c;
-    if (v != 1 || a / 3 + 1 + b + c > kMixedMaxStages) return false;
-    int k = 0;
-    for (; a >= 3; a -= 3) mp->r[k++] = 8;
-    for (int i = 0; i < c; ++i) mp->r[k++] = 5;
-    if (a == 2) mp->r[k++] = 4;
-    for (int i = 0; i < b; ++i) mp->r[k++] = 3;
-    if (a == 1) mp->r[k++] = 2;
-    mp->nst = k;
-    mp->codes = 0;
-    for (int i = 0; i < k; ++i) {
-        const int r = mp->r[i];
-        const uint64_t c = r == 2 ? 0 : r == 3 ? 1 : r == 4 ? 2 : r == 5 ? 3 : 4;
-        mp->codes |= c << (3 * i);
+    while (v % 2 == 0) v /= 2;
+    while (v % 3 == 0) v /= 3;
+    while (v % 5 == 0) v /= 5;
+    if (v != 1 || n < 3) return false;
+    int cur[kMixedMaxStages];
+    int best_len = kMixedMaxStages + 1;
+    std::vector<std::vector<int>> found;
+    mixed_search(n, 0, cur, &best_len, &found);
+    if (found.empty() || best_len > 16) return false;
+    const int64_t nsig = n >= 512 ? 1 : std::min<int64_t>(64, std::max<int64_t>(1, 1536 / n));
+    int64_t best_passes = -1, best_t = 0;
+    int best_min = 0;
+    const std::vector<int> *pick = nullptr;
+    for (const auto &f : found) {
+        int64_t most = 0;
+        int rmin = 16;
+        for (int r : f) {
+            most = std::max<int64_t>(most, nsig * (n / r));
+            rmin = std::min(rmin, r);
+        }
+        const int64_t t = std::min<int64_t>(kMixedMaxThreads, (most + 31) / 32 * 32);
+        int64_t passes = 0;
+        for (int r : f) passes += (nsig * (n / r) + t - 1) / t;
+        if (!pick || passes < best_passes || (passes == best_passes && rmin > best_min)) {
+            pick = &f;
+            best_passes = passes;
+            best_t = t;
+            best_min = rmin;
+        }
     }
+    mp->nst = best_len;
+    mp->codes = 0;
+    for (int i = 0; i < best_len; ++i) {
+        mp->r[i] = (*pick)[i];
+        int c = 0;
+        while (kRadices[c] != mp->r[i]) ++c;
+        mp->codes |= static_cast<uint64_t>(c) << (4 * i);
+    }
+    mp->nsig = static_cast<int>(nsig);
+    mp->threads = static_cast<int>(best_t);
     return true;
 }
 
@@ -280,14 +437,9 @@ int fft_mixed_launch(const void *in, void *out, int64_t n, int64_t batch, int di
     const float2 *tw = nullptr;
     int rc = table_for(n, &tw);
     if (rc != BPLG_OK) return rc;
-    const int nsig = static_cast<int>(n >= 512 ? 1 : std::min<int64_t>(64, (512 + n - 1) / n));
+    const int nsig = mp.nsig;
     const int64_t elems = nsig * n;
-    // one butterfly a thread in the stage of the smallest radix (warps of 32,
-    // at most kMixedMaxThreads)
-    int rmin = 8;
-    for (int i = 0; i < mp.nst; ++i) rmin = std::min(rmin, mp.r[i]);
-    const int threads = static_cast<int>(
-        std::min<int64_t>(kMixedMaxThreads, std::max<int64_t>(32, (elems / rmin + 31) / 32 * 32)));
+    const int threads = mp.threads;
     const int smem = static_cast<int>(2 * elems * static_cast<int64_t>(sizeof(float2)));
     const void *f = dir < 0 ? reinterpret_cast<const void *>(&fft_mixed_kernel<-1>)
                             : reinterpret_cast<const void *>(&fft_mixed_kernel<1>);
