@@ -1,7 +1,8 @@
 """Tuners against exhaustive search on the GPU (Section VI's comparison):
 the learned-cost-model search lands within 5 % of the exhaustive best on a
 small space, and the GB300 cost model (no evaluation) within 15 % on spaces
-of every operation.  Times are re-measured back to back (median of 30
+of every operation, the two-kernel FFT's joint (split, columns, rows per
+block) space included.  Times are re-measured back to back (median of 30
 launches) so the comparison does not rest on the searches' own samples."""
 import pytest
 
@@ -34,7 +35,8 @@ def test_learned_within_five_percent_of_exhaustive_scan_1024(bp):
 
 
 @pytest.mark.parametrize("case", [("scan", 8192, 1 << 13), ("fft", 1024, 1 << 14), ("tridiag", 256, 1 << 16),
-                                  ("tridiag_wm", 1024, 1 << 14), ("refined", 1024, 1 << 13)])
+                                  ("tridiag_wm", 1024, 1 << 14), ("refined", 1024, 1 << 13),
+                                  ("fft", 1 << 18, 1 << 6)])
 def test_cost_model_near_exhaustive(bp, case):
     name, n, batch = case
     op, dt = {"scan": (bp.OP_SCAN, bp.I32), "fft": (bp.OP_FFT, bp.F32), "tridiag": (bp.OP_TRIDIAG, bp.F32),
