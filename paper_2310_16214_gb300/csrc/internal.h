@@ -136,8 +136,9 @@ int stream_scratch(int tag, size_t bytes, cudaStream_t s, void **out);
 // FFT of a length that is not a power of two (fft_bluestein.cu): Bluestein's
 // chirp identity over power-of-two FFTs of size M >= 2n - 1 (plan: one for M,
 // or NULL)
-// mixed-radix Stockham FFT (radices 2, 3, 4, 5, 8, 16) for n = 2^a 3^b 5^c,
-// not a power of two, n <= kMixedMaxN (two signal buffers in shared memory)
+// mixed-radix Stockham FFT (radices 2 .. 16 whose factors are 2, 3, 5) for
+// n = 2^a 3^b 5^c, not a power of two, n <= kMixedMaxN: one compile-time
+// kernel per length (fft_mixed.cuh)
 constexpr int64_t kMixedMaxN = 12288;
 bool fft_mixed_supported(int64_t n);
 int fft_mixed_launch(const void *in, void *out, int64_t n, int64_t batch, int dir, cudaStream_t s);

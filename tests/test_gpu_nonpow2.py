@@ -133,8 +133,8 @@ def test_fft_bluestein_vs_dft(bp, n):
 
 
 # 2^a 3^b 5^c (not a power of two, at most 12288): the mixed-radix Stockham
-# kernel, radices 16, 8, 5, 4, 3, 2; odd lengths take the 8-byte load path,
-# small ones several signals a block (ragged last block)
+# kernels (one per length, radices 2 .. 16); small lengths several signals a
+# block (ragged last block)
 @pytest.mark.parametrize("n", [3, 5, 6, 9, 10, 12, 15, 20, 25, 27, 45, 60, 81, 100, 120, 125, 243, 360, 375, 625,
                                1000, 1215, 1536, 2187, 3000])
 def test_fft_mixed_radix_vs_dft(bp, n):
@@ -144,6 +144,42 @@ def test_fft_mixed_radix_vs_dft(bp, n):
         X = run_fft(bp, x, direction)
         ref = oracle.dft(x, direction)
         assert fft_rel_err(X, ref).max() <= tol(n), (n, direction)
+
+
+def test_fft_mixed_radix_every_length(bp):
+    """Every length with a compile-time kernel (all 2^a 3^b 5^c up to 12288
+    that are not powers of two), both directions.  Below 1000 points: three
+    signals (a partly filled block) against the O(N^2) oracle.  From 1000 on
+    (where the O(N^2) oracle would take minutes): an impulse against its
+    closed form exp(dir 2 pi i j0 k / n) and a random signal against numpy's
+    float64 FFT."""
+    def smooth(v):
+        for p in (2, 3, 5):
+            while v % p == 0:
+                v //= p
+        return v == 1
+    lengths = [n for n in range(3, 12289) if smooth(n) and n & (n - 1)]
+    assert len(lengths) == 172
+    for n in lengths:
+        if n < 1000:
+            x = si.fft_c64(3, n, stream=5000 + n)
+            for direction in (-1, 1):
+                X = run_fft(bp, x, direction)
+                assert fft_rel_err(X, oracle.dft(x, direction)).max() <= tol(n), (n, direction)
+            continue
+        k = np.arange(n, dtype=np.float64)
+        j0 = (7919 * n) // 9973
+        imp = np.zeros((1, n), np.complex64)
+        imp[0, j0] = 1
+        x = si.fft_c64(1, n, stream=5000 + n)
+        for direction in (-1, 1):
+            X = run_fft(bp, imp, direction).astype(np.complex128)
+            ref = np.exp(direction * 2j * np.pi * ((j0 * k) % n) / n)[None, :]
+            assert fft_rel_err(X, ref).max() <= tol(n), (n, direction)
+            Y = run_fft(bp, x, direction)
+            xd = x.astype(np.complex128)
+            ref = np.fft.fft(xd, axis=-1) if direction < 0 else np.fft.ifft(xd, axis=-1) * n
+            assert fft_rel_err(Y, ref).max() <= tol(n), (n, direction)
 
 
 @pytest.mark.parametrize("n", [3125, 6000, 10000, 12288])
