@@ -280,7 +280,9 @@ constexpr Plan mixed_plan(int n) {
     for (int spb = 1; spb <= max_spb; ++spb) {
         const int threads = (spb * p.t + 31) / 32 * 32;
         if (spb * sm1 > kSmemPerBlock) break;
-        for (int regs = 64; regs >= lower || regs == 64; regs -= 8) {
+        // budgets of 64, 56, 48 or 32 registers (at 40 the compiler spilled
+        // the 10 x 10 x 10 kernel, slowing it by a fifth)
+        for (int regs = 64; regs >= lower || regs == 64; regs -= (regs == 48 ? 16 : 8)) {
             const int r = regs > lower ? regs : lower;
             const int blocks = blocks_per_sm(threads, spb * sm1, r);
             const int busy = blocks * spb * p.t;
