@@ -180,11 +180,12 @@ int bplg_scan_batched(int32_t dtype, const void *in, void *out, int64_t n, int64
  *          and stream and grows when needed (a growth waits for the stream);
  *          in may equal out.
  *          A length n = 2^a 3^b 5^c up to 12288 that is not a power of two
- *          (and no plan) runs a mixed-radix Stockham kernel: stages of
- *          radix 8, 5, 4, 3 and 2, the block's signals in shared memory,
- *          the stage twiddles from a per-n table W_n^e made on the first
- *          call with that n (float64 on the host, rounded to float32,
- *          uploaded synchronously).
+ *          (and no plan) runs a mixed-radix Stockham kernel compiled for
+ *          that length: stages of radix 2, 3, 4, 5, 6, 8, 9, 10, 12, 15 or
+ *          16, the block's signals in shared memory, the stage twiddles
+ *          from a per-n table W_n^e made on the first call with that n
+ *          (float64 on the host, rounded to float32, uploaded
+ *          synchronously).
  *          Any other length that is not a power of two runs Bluestein's
  *          chirp identity: X_k = h_k sum_j (x_j h_j) conj(h_{k-j}) with
  *          h_m = exp(dir pi i m^2 / n), a cyclic convolution of length
