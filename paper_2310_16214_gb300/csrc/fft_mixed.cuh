@@ -1,5 +1,5 @@
 // Mixed-radix Stockham FFT for lengths n = 2^a 3^b 5^c that are not powers
-// of two (at most kMixedMaxN), one kernel per length with its whole stage
+// of two (at most 12288), one kernel per length with its whole stage
 // schedule fixed at compile time.  (The paper keeps to N = r^n; this extends
 // the radix-r Stockham formulation of Section III to products of small
 // radices, so such lengths need not go through Bluestein's identity.)
@@ -27,11 +27,11 @@
 // non-increasing order; T threads per signal, each doing at most B
 // butterflies a stage (B = 1 unless n / r_min exceeds 1024 threads); S
 // signals a block and a register budget, chosen for small blocks and
-// enough busy threads per SM.  The signals sit in one shared-memory buffer (n complex
-// values each) -- a stage reads its inputs into registers, the block waits,
-// and writes its outputs in place -- or in two that the stages alternate
-// between, where that costs no block per SM; the first stage reads global
-// memory and the last writes it.
+// enough busy threads per SM.  The signals sit in one shared-memory buffer
+// (n complex values each) -- a stage reads its inputs into registers, the
+// block waits, and writes its outputs in place -- or in two that the stages
+// alternate between, where that costs no block per SM; the first stage
+// reads global memory and the last writes it.
 #pragma once
 
 #include <stddef.h>
@@ -254,8 +254,8 @@ constexpr Plan mixed_plan(int n) {
     // Block shape and register budget.  The budget is at least what the
     // values held across a barrier need (two registers each, plus room for
     // indices, addresses and the codelets' temporaries; 48 for the 12- to
-    // 16-point codelets, which need them to keep their loads in flight).  Blocks of at most 256 threads where a signal
-    // allows: many small blocks, so that one block's barriers stall few
+    // 16-point codelets, which need them to keep their loads in flight).
+    // Blocks of at most 256 threads where a signal allows: many small blocks, so that one block's barriers stall few
     // threads and the blocks of an SM drift apart, some loading while others
     // compute.  Among the shapes that keep at least 1280 threads (40 warps)
     // of an SM busy, the largest budget (fewer registers cost loads in
