@@ -25,7 +25,9 @@
 // code of its own radices only (so its registers are those of its largest
 // codelet).  The plan (mixed_plan below): the fewest stages, radices in
 // non-increasing order; T threads per signal, each doing at most B
-// butterflies a stage (B = 1 unless n / r_min exceeds 1024 threads); S
+// butterflies a stage (one in the smallest-radix stage unless n / r_min
+// exceeds 1024 threads, or one in the largest-radix stage when the radices
+// are at least a factor two apart); S
 // signals a block and a register budget, chosen for small blocks and
 // enough busy threads per SM.  The signals sit in one shared-memory buffer
 // (n complex values each) -- a stage reads its inputs into registers, the
@@ -243,9 +245,18 @@ constexpr void search(int n, int left, int from, Plan &cur, Plan &best) {
 constexpr Plan mixed_plan(int n) {
     Plan cur{}, p{};
     search(n, n, 0, cur, p);
-    const int rmin = rmin_of(p);
-    p.b = bfly_per_thread(n, rmin);
-    p.t = (n / rmin + p.b - 1) / p.b;
+    const int rmin = rmin_of(p), rmax0 = rmax_of(p);
+    if (rmax0 >= 2 * rmin && n / rmax0 <= kMaxThreads) {
+        // radices at least a factor two apart: one butterfly a thread in the
+        // largest-radix stage and several in the smaller-radix ones, rather
+        // than idle threads in the large one (measured faster at n = 375,
+        // 2000 and 3000; slower at 1620 and 6000, whose radices are closer)
+        p.t = n / rmax0;
+        p.b = (n / rmin + p.t - 1) / p.t;
+    } else {
+        p.b = bfly_per_thread(n, rmin);
+        p.t = (n / rmin + p.b - 1) / p.b;
+    }
     p.vmax = 0;
     for (int s = 0; s < p.k; ++s) {
         const int bs = (n / p.r[s] + p.t - 1) / p.t;
